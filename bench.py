@@ -1,0 +1,408 @@
+"""Benchmark: wire-scan depth reconstruction on GB300.
+
+Default workload (one "step" = one full reconstruction of one scan):
+2048x2048-pixel detector, 401 wire steps, 1001 depth bins of 1 um over
+[-500, 500] um; uint16 images [401][2048][2048] (3.36 GB) resident in HBM,
+FP32 output [1001][2048][2048] (16.8 GB).  Both exceed the 129 MB L2, so no
+flush is needed between steps.  Synthetic forward-model scan (200 Gaussian
+spots at seeded depths, Poisson background 20), standing in for the paper's
+HDF5 beamline scans.
+
+Prints ONE JSON line (rank 0).  `value` is pixel*steps/s over all ranks (each
+rank reconstructs its own scan: replicas, weak scaling); `e2e` is the same
+metric through dr_reconstruct_host with pinned host buffers (host->device
+upload and device->host download of the whole result inside the timed
+region); `roofline` compares the kernel's algorithmic bytes per launch with
+the measured HBM copy bandwidth; `cpu_baseline` times the FP64 CPU oracle on
+a bounded sample of rows of the same scan.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pixel·steps/s and % of HBM peak; served scans/s with p50/p99 latency"
+UNIT = "pixel·steps/s"
+WORKLOAD = ("plain method, full detector: 2048x2048 uint16 pixels, 401 wire steps of 1 um, "
+            "1001 bins of 1 um over [-500,500] um, FP32 output [1001][2048][2048], "
+            "device-resident input")
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "rows_kernel_full_detector_traffic.txt")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("dr_recon.cu", "dr_internal.h"):
+        with open(os.path.join(ROOT, "paper_2201_13309_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    try:
+        kv = {}
+        for line in open(PROFILE_TRAFFIC):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """Samples SM clock and clock-event reasons through NVML while running."""
+
+    REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x100: "display_clock_setting"}
+
+    def __init__(self, index, uuid=None, period=0.005):
+        self.samples = []
+        self.period = period
+        self.ok = False
+        self.max_mhz = None
+        try:
+            self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nv.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            found = False
+            if uuid:
+                u = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+                found = self.nv.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(self.h)) == 0
+            if not found and self.nv.nvmlDeviceGetHandleByIndex_v2(
+                    index, ctypes.byref(self.h)) != 0:
+                return
+            m = ctypes.c_uint()
+            if self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(m)) == 0:
+                self.max_mhz = int(m.value)
+            self.ok = True
+        except OSError:
+            pass
+
+    def _read(self):
+        c = ctypes.c_uint()
+        r = ctypes.c_ulonglong()
+        self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(c))
+        fn = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        fn(self.h, ctypes.byref(r))
+        return int(c.value), int(r.value)
+
+    def _loop(self):
+        while not self._stop.is_set():
+            self.samples.append(self._read())
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.ok:
+            self._stop = threading.Event()
+            self._t = threading.Thread(target=self._loop, daemon=True)
+            self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            self._stop.set()
+            self._t.join()
+            self.samples.append(self._read())
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"],
+                    "samples": 0}
+        mhz = [c for c, _ in self.samples]
+        mask = 0
+        for _, r in self.samples:
+            mask |= r
+        reasons = [n for b, n in self.REASONS.items() if mask & b and n != "gpu_idle"]
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_sample(spec, host_rows, rows_idx, threads, budget_s=None):
+    """Time the FP64 oracle on the given rows (one-row geometries)."""
+    from oracle import oracle as O
+
+    t0 = time.perf_counter()
+    for r, img in zip(rows_idx, host_rows):
+        g = dict(spec.geom)
+        g["det_origin"] = (np.asarray(spec.geom["det_origin"])
+                           + r * np.asarray(spec.geom["row_step"])).tolist()
+        g["rows"] = 1
+        O.reconstruct(g, spec.wires, img, spec.edges, threads=threads)
+        if budget_s and time.perf_counter() - t0 > budget_s:
+            break
+    return time.perf_counter() - t0
+
+
+def synth_rows_host(spec, rows_idx, seed=0):
+    """uint16 [K, 1, W] stacks of the chosen rows, generated on the host with
+    the same forward model as the device scan (spots + Poisson background)."""
+    from paper_2201_13309_gb300 import synth
+
+    rng = np.random.Generator(np.random.PCG64(seed + 12345))
+    idx, val = synth.spot_contributions(spec.geom, spec.wires, spec.scat)
+    H, W, K = spec.geom["rows"], spec.geom["cols"], spec.K
+    out = []
+    kk = idx // (H * W)
+    rr = (idx // W) % H
+    cc = idx % W
+    for r in rows_idx:
+        rate = np.full((K, 1, W), 20.0)
+        sel = rr == r
+        np.add.at(rate, (kk[sel], 0, cc[sel]), val[sel])
+        out.append(synth.poisson_u16(rng, rate))
+    return out
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the FP64 CPU oracle as it stands, on host cores."""
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2201_13309_gb300 import synth
+
+    O.build()
+    spec = synth.full_scan_spec(0)
+    threads = os.cpu_count() or 1
+    rows_per_step = max(1, threads // 4)
+    pool_idx = [int(r) for r in np.linspace(0, 2047, 32)]
+    pool = synth_rows_host(spec, pool_idx)
+    times = []
+    for s in range(args.warmup + args.steps):
+        pick = [(s * rows_per_step + i) % len(pool_idx) for i in range(rows_per_step)]
+        dt = cpu_oracle_sample(spec, [pool[i] for i in pick], [pool_idx[i] for i in pick],
+                               threads)
+        if s >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    units = rows_per_step * spec.geom["cols"] * spec.K * args.steps
+    value = units / tot
+    sample = (f"{rows_per_step} detector rows per step ({rows_per_step * 2048} pixels x 401 "
+              f"steps x 1001 bins), FP64, {threads} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--rows", type=int, default=2048,
+                    help="reconstruct only the first ROWS detector rows (small profiling case)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+
+    import __graft_entry__
+    from paper_2201_13309_gb300 import dr, synth
+
+    if world > 1:
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        tdist.barrier()
+        __graft_entry__.build()
+
+    spec = synth.full_scan_spec(0)
+    if args.rows != spec.geom["rows"]:
+        spec.geom = dict(spec.geom, rows=args.rows)
+        keep = spec.scat.spot_row < args.rows - 2
+        spec.scat = synth.Scatterers(spec.scat.depth[keep], spec.scat.peak[keep],
+                                     spec.scat.spot_row[keep], spec.scat.spot_col[keep])
+    images = synth.device_spot_images(spec.geom, spec.wires, spec.scat, seed=rank, background=20.0,
+                                      device=dev)
+    plan = dr.Plan(spec.geom, spec.wires, spec.edges)
+    info = plan.info()
+    out = plan.empty_output(dev)
+    stream = torch.cuda.Stream(dev)
+    P = spec.P
+    units_per_step = P * spec.K
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.reconstruct(images, out, stream=stream)
+    barrier()
+    plan.check_device()
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(dev.index, uuid)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with sampler:
+        start.record(stream)
+        for _ in range(args.steps):
+            plan.reconstruct(images, out, stream=stream)
+        stop.record(stream)
+        stop.synchronize()
+    barrier()
+    plan.check_device()
+    elapsed_ms = start.elapsed_time(stop)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * units_per_step * args.steps / (elapsed_ms * 1e-3)
+
+    # kernel roofline: one launch per step, so the event time per step is
+    # the kernel's average launch duration
+    peak, peak_kind = measured_hbm_peak()
+    alg_bytes = info["bytes_per_call"]
+    achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": peak_kind, "kernel": "rows_kernel<GeoFx,float,tma,4>",
+                "algorithmic_bytes_per_launch": alg_bytes}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        h_img = torch.empty(images.shape, dtype=torch.int16, pin_memory=True)
+        h_img.copy_(images)
+        h_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+        for _ in range(1):
+            plan.reconstruct_host(h_img, h_out, images, out, stream=stream)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            plan.reconstruct_host(h_img, h_out, images, out, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * units_per_step * args.e2e_steps / (e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(images.numel() * 2),
+               "d2h_bytes_per_step": int(out.numel() * out.element_size()),
+               "steps": args.e2e_steps, "ms_per_step": e2e_ms / args.e2e_steps}
+        del h_img, h_out
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        from oracle import oracle as O
+
+        O.build()
+        threads = os.cpu_count() or 1
+        probe = [1023]
+        host = synth_rows_host(spec, probe)
+        t1 = cpu_oracle_sample(spec, host, probe, threads)
+        n = max(1, min(512, int(args.cpu_seconds / max(t1, 1e-3))))
+        rows_idx = [int(r) for r in np.linspace(0, 2047, n)]
+        host = synth_rows_host(spec, rows_idx)
+        dt = cpu_oracle_sample(spec, host, rows_idx, threads)
+        cpu = {"value": len(rows_idx) * spec.geom["cols"] * spec.K / dt, "unit": UNIT,
+               "cores": threads, "kind": "oracle",
+               "sample": (f"{len(rows_idx)} of 2048 detector rows ({len(rows_idx) * 2048} pixels "
+                          f"x 401 steps x 1001 bins), FP64, {threads} threads, {dt:.1f} s")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.rows == 2048 else
+                       WORKLOAD + f" (first {args.rows} rows only)", "pixels": P, "wire_steps": spec.K,
+                       "bins": spec.B, "parallelism": f"replicas x{world}",
+                       "l2": f"input ({2 * units_per_step / 1e9:.2f} GB) and output "
+                             f"({4 * P * spec.B / 1e9:.1f} GB) larger than L2; no flush",
+                       "kernel": info["kernel"], "tile_cols": info["tile_cols"],
+                       "pixels_per_thread": info["pixels_per_thread"],
+                       "bin_groups": info["bin_groups"], "threads": info["threads"],
+                       "smem_bytes": info["smem_bytes"]},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": sampler.summary(),
+            "hbm_frac": roofline["frac"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,175 @@
+/*
+ * dr.h -- C ABI of the GB300 wire-scan depth reconstruction library (libdr).
+ *
+ * Method: differential-aperture depth reconstruction (the paper's Sec. III:
+ * per pixel, the intensity difference between consecutive wire-step images is
+ * assigned to depth and summed into a depth-resolved result; Sec. III-C
+ * "pixel reconstruction function").  For every detector pixel and wire step k
+ * the library computes the beam depth d_k at which the ray from that pixel
+ * grazes the chosen wire edge (tangent to the wire circle in the plane
+ * perpendicular to the wire axis, intersected with the incident beam), takes
+ * the exact integer difference dI_k = I_k - I_{k+1}, and spreads dI_k over
+ * the output depth bins in proportion to the overlap of [d_k, d_{k+1}] with
+ * each bin.  Mass outside [e_0, e_B] is dropped.
+ *
+ * Units: lengths in millimetres, lab frame.  Depth is the signed distance
+ * along beam_dir (normalised internally) from beam_origin.
+ *
+ * Layouts (row-major, no padding):
+ *   images  [K][rows][cols]  uint16   (Sec. III-B: p images of m rows x n cols,
+ *                                      stored as one flat array, the "1D array")
+ *   output  [B][rows][cols]  float32 or bfloat16 (plan option)
+ *
+ * Ownership: a plan owns its device constants; the caller owns every image and
+ * output buffer.  Device pointers must come from cudaMalloc (or torch) on the
+ * current device.  No call throws; every call returns a dr_status, and
+ * dr_last_error() gives a one-line explanation of the last failure on the
+ * calling thread.  Kernels are launched asynchronously on the caller's stream.
+ */
+#ifndef DR_H_
+#define DR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; 0 is the legacy default stream. */
+typedef struct CUstream_st *dr_stream_t;
+
+typedef enum {
+  DR_OK = 0,
+  DR_ERR_INVALID_ARG = 1,   /* null pointer, bad size, unsorted bin edges */
+  DR_ERR_GEOMETRY = 2,      /* beam along the wire, pixel inside the wire, wire
+                               not between beam and detector, no travel */
+  DR_ERR_NONMONOTONIC = 3,  /* depth sequence of some pixel not strictly
+                               monotone in the step index */
+  DR_ERR_OOM = 4,           /* device or host allocation failed */
+  DR_ERR_BUDGET = 5,        /* request does not fit the memory budget */
+  DR_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+  DR_ERR_TIMEOUT = 7,       /* a kernel gave up waiting (bounded wait) */
+  DR_ERR_UNSUPPORTED = 8    /* valid request outside what this build handles */
+} dr_status;
+
+enum { DR_EDGE_LEADING = 0, DR_EDGE_TRAILING = 1 };
+enum { DR_OUT_F32 = 0, DR_OUT_BF16 = 1 };
+enum { DR_GEOM_FP32 = 0, DR_GEOM_FP64 = 1 };
+enum { DR_KERNEL_ROWS = 0, DR_KERNEL_PIXELS = 1 };
+
+/* Scan geometry.  Pixel (r, c) has its centre at
+ * det_origin + r*row_step + c*col_step.  The wire is an infinite cylinder of
+ * radius wire_radius whose axis runs along wire_axis through each wire centre.
+ * edge selects the wire edge whose passage is reconstructed: the leading edge
+ * (the one moving in the direction of travel; a pixel's intensity drops as it
+ * covers a scatterer) or the trailing edge (intensity comes back). */
+typedef struct {
+  double beam_origin[3];
+  double beam_dir[3];
+  double det_origin[3];
+  double row_step[3];
+  double col_step[3];
+  int32_t rows;
+  int32_t cols;
+  double wire_axis[3];
+  double wire_radius;
+  int32_t edge;
+} dr_geometry;
+
+/* Optional plan settings; a null pointer means all zero (defaults). */
+typedef struct {
+  int32_t out_dtype;        /* DR_OUT_F32 (default) or DR_OUT_BF16 */
+  int32_t geom_precision;   /* DR_GEOM_FP32 (default): per-step depth in FP32
+                               on FP64 per-pixel constants; DR_GEOM_FP64: the
+                               whole depth computation in FP64 on the GPU */
+  int32_t tile_cols;        /* pixels per CTA along a row; 0 = tuned */
+  int32_t bin_groups;       /* warps-groups splitting the bins; 0 = tuned */
+  int32_t force_pixels;     /* 1: use the per-pixel kernel even when all
+                               pixels of a row share their depths */
+  int32_t reserved[3];
+} dr_plan_options;
+
+typedef struct dr_plan dr_plan_t;
+
+/* What a plan decided (for reports and tests). */
+typedef struct {
+  int32_t rows, cols, K, B;
+  int32_t kernel;           /* DR_KERNEL_ROWS or DR_KERNEL_PIXELS */
+  int32_t tile_cols, pixels_per_thread, bin_groups, threads;
+  int32_t smem_bytes, tma_chunk, tma_chunks;
+  int32_t out_dtype, geom_precision, edge, reversed;
+  int32_t fixed_shift;      /* depth positions in units of 2^-fixed_shift mm
+                               of projected depth (FP32 geometry) */
+  double depth_min, depth_max;   /* range of all d_k (mm) */
+  double min_step;               /* smallest |d_{k+1} - d_k| (mm) */
+  size_t device_bytes;           /* device memory held by the plan */
+  double bytes_per_call;         /* algorithmic HBM bytes of one
+                                    dr_reconstruct: 2*P*K + out*P*B */
+} dr_plan_info;
+
+/* Build a plan: validate the geometry, compute the per-pixel (or per-row,
+ * when all pixels of a row share their depths) constants in FP64, check that
+ * every depth sequence is strictly monotone, upload the constants and pick the
+ * kernel and tile shape.
+ *   wire_centres  host [K][3] FP64, K >= 2
+ *   bin_edges     host [B+1] FP64 strictly increasing (depth, mm), B >= 1
+ * rows or cols may be 0 (an empty ROI: dr_reconstruct then does nothing).
+ * Allocates device memory on the current device; *out is null on failure. */
+dr_status dr_plan(const dr_geometry *geometry, const double *wire_centres,
+                  int32_t K, const double *bin_edges, int32_t B,
+                  const dr_plan_options *options, dr_plan_t **out);
+
+/* Free a plan (null is ignored).  The caller must make sure no kernel that
+ * uses the plan is still running. */
+void dr_plan_destroy(dr_plan_t *plan);
+
+dr_status dr_plan_get_info(const dr_plan_t *plan, dr_plan_info *info);
+size_t dr_plan_device_bytes(const dr_plan_t *plan);
+
+/* Reconstruct one scan: d_images [K][rows][cols] uint16 in device memory,
+ * d_out [B][rows][cols] (float or bf16 per the plan) in device memory.  Every
+ * output element is written exactly once (no prior clearing needed).  Allocates
+ * nothing; asynchronous on stream.  A plan may be used from several streams at
+ * once.  Input rows whose byte pitch is a multiple of 16 and a 16-byte aligned
+ * d_images are staged by TMA; other inputs take a plain-load path. */
+dr_status dr_reconstruct(const dr_plan_t *plan, const uint16_t *d_images,
+                         void *d_out, dr_stream_t stream);
+
+/* End-to-end form with host buffers: copies h_images (pinned host memory for
+ * full speed) into the caller's device buffer d_images_ws, reconstructs into
+ * d_out_ws, and copies the result into h_out, all in order on stream.  The
+ * call returns once everything is queued; synchronize the stream before
+ * reading h_out.  Sizes are those of dr_reconstruct. */
+dr_status dr_reconstruct_host(const dr_plan_t *plan, const uint16_t *h_images,
+                              void *h_out, uint16_t *d_images_ws,
+                              void *d_out_ws, dr_stream_t stream);
+
+/* The exact integer differences the kernels use (Sec. III-C "difference
+ * intensity at each pixel"): d_diff[k][p] = images[k][p] - images[k+1][p] as
+ * int32, k = 0..K-2, for a [K][rows][cols] uint16 device stack. */
+dr_status dr_image_differences(const uint16_t *d_images, int32_t K,
+                               int32_t rows, int32_t cols, int32_t *d_diff,
+                               dr_stream_t stream);
+
+/* The depths d_k (mm) the plan's kernels use, for rows r0 .. r0+nrows-1:
+ * d_depths [nrows][cols][K] FP64 in device memory.  Computed on the GPU by the
+ * same device code as dr_reconstruct (for checks against the oracle). */
+dr_status dr_plan_depths(const dr_plan_t *plan, int32_t r0, int32_t nrows,
+                         double *d_depths, dr_stream_t stream);
+
+/* Read and clear the plan's device error word (set by a kernel whose bounded
+ * wait ran out).  Synchronizes the device.  DR_OK or DR_ERR_TIMEOUT. */
+dr_status dr_plan_check(const dr_plan_t *plan);
+
+const char *dr_status_string(dr_status status);
+/* One line describing the last failure on the calling thread ("" if none). */
+const char *dr_last_error(void);
+/* Library version, e.g. "1.0.0". */
+const char *dr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DR_H_ */

@@ -1,0 +1,572 @@
+// Plan builder: FP64 per-pixel (or per-row) geometry constants, validation,
+// device upload and launch-shape choice.  Host code.
+//
+// The depth model is the tangent condition described in dr_internal.h.  The
+// plan computes, in FP64, the projected frame, the per-group constants
+// (D, L0, Q0), the per-step constants (z_k, eta_k), every depth sequence
+// needed for the monotonicity check, and the fixed-point scale that makes
+// the kernels' position differences exact.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "dr_internal.h"
+
+namespace dr {
+
+static thread_local char g_msg[512];
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+}
+
+dr_status cuda_fail(const char *what, int err) {
+  set_error("%s: %s", what, cudaGetErrorString((cudaError_t)err));
+  return DR_ERR_CUDA;
+}
+
+namespace {
+
+struct V3 {
+  double x, y, z;
+};
+V3 v3(const double *p) { return {p[0], p[1], p[2]}; }
+V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+double norm(V3 a) { return std::sqrt(dot(a, a)); }
+bool finite3(const double *p) {
+  return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]);
+}
+
+// FP64 solution of the tangent condition for one (group, step): projected
+// depth t.  Fixed point on the exact form t = z + Q0 + (a + sR dL(t))/(D-eta);
+// the map contracts by ~R/D per pass, three passes reach rounding level.
+double solve_t(double Y, double Z, double y0, double sR, double D, double L0,
+               double Q0, double z, double eta) {
+  double Dm = D - eta;
+  double a = y0 * z + eta * (z - Z + Q0);
+  double t = z + Q0 + a / Dm;
+  for (int it = 0; it < 3; ++it) {
+    double u = Z - t;
+    double L = std::sqrt(Y * Y + u * u);
+    double dL = t * (t - 2.0 * Z) / (L + L0);
+    t = z + Q0 + (a + sR * dL) / Dm;
+  }
+  return t;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+}  // namespace dr
+
+using namespace dr;
+
+namespace {
+
+struct Group64 {
+  double Y, Z, D, L0, Q0;
+};
+
+// Launch shape: smem layout sizes for the two kernels (see dr_recon.cu).
+int rows_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64) {
+  size_t s = 128;                                          // mbarrier slot
+  s += align_up((size_t)Kpad * tile_cols * 2, 16);         // image tile
+  s += align_up((size_t)K * (f64 ? 8 : 4), 16);            // depth positions
+  s += align_up((size_t)(B + 1) * 8, 16);                  // (k, f) table
+  return (int)s;
+}
+
+int pixels_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64) {
+  size_t s = 128;
+  s += align_up((size_t)Kpad * tile_cols * 2, 16);
+  s += align_up((size_t)K * 16, 16);                       // step constants
+  s += align_up((size_t)(B + 1) * (f64 ? 8 : 4), 16);      // edges
+  return (int)s;
+}
+
+void choose_chunks(int K, int *kc, int *nchunks) {
+  int nmin = (K + 255) / 256;
+  int best_n = nmin, best_pad = 1 << 30;
+  for (int n = nmin; n <= nmin + 4; ++n) {
+    int c = (K + n - 1) / n;
+    int pad = n * c - K;
+    if (pad < best_pad) {
+      best_pad = pad;
+      best_n = n;
+    }
+  }
+  *nchunks = best_n;
+  *kc = (K + best_n - 1) / best_n;
+}
+
+constexpr int kSmemPerSm = 228 * 1024;
+constexpr int kSmemPerCtaMax = 227 * 1024;
+
+}  // namespace
+
+extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires,
+                             int32_t K, const double *edges, int32_t B,
+                             const dr_plan_options *opt_in, dr_plan_t **out) {
+  if (out) *out = nullptr;
+  if (!g || !wires || !edges || !out) {
+    set_error("dr_plan: null argument");
+    return DR_ERR_INVALID_ARG;
+  }
+  dr_plan_options opt;
+  std::memset(&opt, 0, sizeof(opt));
+  if (opt_in) opt = *opt_in;
+  if (K < 2 || B < 1 || g->rows < 0 || g->cols < 0) {
+    set_error("dr_plan: need K >= 2, B >= 1, rows, cols >= 0 (K=%d B=%d)", K, B);
+    return DR_ERR_INVALID_ARG;
+  }
+  if (g->rows > 65535) {
+    set_error("dr_plan: rows > 65535 not supported");
+    return DR_ERR_UNSUPPORTED;
+  }
+  if (g->edge != DR_EDGE_LEADING && g->edge != DR_EDGE_TRAILING) {
+    set_error("dr_plan: edge must be DR_EDGE_LEADING or DR_EDGE_TRAILING");
+    return DR_ERR_INVALID_ARG;
+  }
+  if ((opt.out_dtype != DR_OUT_F32 && opt.out_dtype != DR_OUT_BF16) ||
+      (opt.geom_precision != DR_GEOM_FP32 && opt.geom_precision != DR_GEOM_FP64) ||
+      opt.tile_cols < 0 || opt.bin_groups < 0) {
+    set_error("dr_plan: bad options");
+    return DR_ERR_INVALID_ARG;
+  }
+  for (int j = 0; j <= B; ++j) {
+    if (!std::isfinite(edges[j]) || (j > 0 && !(edges[j] > edges[j - 1]))) {
+      set_error("dr_plan: bin edges must be finite and strictly increasing (j=%d)", j);
+      return DR_ERR_INVALID_ARG;
+    }
+  }
+  for (int k = 0; k < K; ++k)
+    if (!finite3(wires + 3 * k)) {
+      set_error("dr_plan: wire centre %d not finite", k);
+      return DR_ERR_INVALID_ARG;
+    }
+  if (!finite3(g->beam_origin) || !finite3(g->beam_dir) || !finite3(g->det_origin) ||
+      !finite3(g->row_step) || !finite3(g->col_step) || !finite3(g->wire_axis) ||
+      !std::isfinite(g->wire_radius) || !(g->wire_radius > 0.0)) {
+    set_error("dr_plan: geometry not finite or radius <= 0");
+    return DR_ERR_INVALID_ARG;
+  }
+
+  // ---- projected frame ----
+  V3 ax = v3(g->wire_axis), bd = v3(g->beam_dir), O = v3(g->beam_origin);
+  if (!(norm(ax) > 0) || !(norm(bd) > 0)) {
+    set_error("dr_plan: zero wire axis or beam direction");
+    return DR_ERR_GEOMETRY;
+  }
+  ax = (1.0 / norm(ax)) * ax;
+  bd = (1.0 / norm(bd)) * bd;
+  V3 bp = bd - dot(bd, ax) * ax;
+  double nb = norm(bp);
+  if (!(nb > 1e-9)) {
+    set_error("dr_plan: beam runs along the wire axis");
+    return DR_ERR_GEOMETRY;
+  }
+  V3 e2 = (1.0 / nb) * bp;
+  V3 c0 = v3(wires) - O;
+  V3 w = c0 - dot(c0, ax) * ax;
+  w = w - dot(w, e2) * e2;
+  if (!(norm(w) > 0)) {
+    set_error("dr_plan: first wire centre lies on the beam");
+    return DR_ERR_GEOMETRY;
+  }
+  V3 e1 = (1.0 / norm(w)) * w;
+  const double R = g->wire_radius;
+
+  std::vector<double> yk(K), zk(K);
+  for (int k = 0; k < K; ++k) {
+    V3 c = v3(wires + 3 * k) - O;
+    yk[k] = dot(c, e1);
+    zk[k] = dot(c, e2);
+  }
+  const double y0 = yk[0];
+  const double travel = zk[K - 1] - zk[0];
+  if (travel == 0.0) {
+    set_error("dr_plan: wire does not travel along the projected beam");
+    return DR_ERR_GEOMETRY;
+  }
+  const bool reverse = travel < 0.0;
+  const double sgn = (reverse ? -1.0 : 1.0) * (g->edge == DR_EDGE_LEADING ? 1.0 : -1.0);
+  const double sR = sgn * R;
+  bool has_eta = false;
+  double ymin = yk[0], ymax = yk[0];
+  for (int k = 0; k < K; ++k) {
+    has_eta |= (yk[k] != y0);
+    ymin = std::min(ymin, yk[k]);
+    ymax = std::max(ymax, yk[k]);
+  }
+  if (!(ymin > R)) {
+    set_error("dr_plan: wire overlaps the beam (distance %.6g <= radius)", ymin);
+    return DR_ERR_GEOMETRY;
+  }
+
+  const int H = g->rows, W = g->cols;
+  const long long P = (long long)H * W;
+  V3 dorg = v3(g->det_origin) - O, rs = v3(g->row_step), cs = v3(g->col_step);
+  // pixel coordinates are affine in (r, c): Y = Y00 + r*Yr + c*Yc
+  double Y00 = dot(dorg, e1), Z00 = dot(dorg, e2);
+  double Yr = dot(rs, e1), Zr = dot(rs, e2), Yc = dot(cs, e1), Zc = dot(cs, e2);
+  if (P > 0) {
+    double Ymin = 1e300;
+    for (int cr = 0; cr < 4; ++cr) {
+      double r = (cr & 1) ? H - 1 : 0, c = (cr & 2) ? W - 1 : 0;
+      Ymin = std::min(Ymin, Y00 + r * Yr + c * Yc);
+    }
+    if (!(Ymin - ymax > R)) {
+      set_error("dr_plan: wire not between beam and detector (min gap %.6g mm)",
+                Ymin - ymax);
+      return DR_ERR_GEOMETRY;
+    }
+  }
+  double cs_n = norm(cs);
+  bool rows_shared = std::fabs(Yc) + std::fabs(Zc) <= 1e-13 * std::max(cs_n, 1e-300);
+  if (opt.force_pixels) rows_shared = false;
+  if (W == 0 || H == 0) rows_shared = true;
+
+  const int G = rows_shared ? H : (int)P;
+  if (!rows_shared && P > (1LL << 31) / 2) {
+    set_error("dr_plan: too many pixels for the per-pixel kernel");
+    return DR_ERR_UNSUPPORTED;
+  }
+  std::vector<Group64> grp(G);
+  for (int i = 0; i < G; ++i) {
+    double r = rows_shared ? i : i / W, c = rows_shared ? 0 : i % W;
+    Group64 q;
+    q.Y = Y00 + r * Yr + c * Yc;
+    q.Z = Z00 + r * Zr + c * Zc;
+    q.D = q.Y - y0;
+    q.L0 = std::sqrt(q.Y * q.Y + q.Z * q.Z);
+    q.Q0 = (-y0 * q.Z + sR * q.L0) / q.D;
+    grp[i] = q;
+  }
+
+  // Steps in processing order (increasing depth).
+  std::vector<double> zp(K), ep(K);
+  for (int k = 0; k < K; ++k) {
+    int src = reverse ? K - 1 - k : k;
+    zp[k] = zk[src];
+    ep[k] = yk[src] - y0;
+  }
+
+  // ---- FP64 depth sequences: monotonicity, range, smallest step ----
+  // Row groups: every (group, step).  Pixel groups: every pixel at the first
+  // and last step (the range) and a sub-grid of pixels at every step.
+  double tmin = 1e300, tmax = -1e300, minstep = 1e300, remmax = 0.0;
+  auto check_group = [&](const Group64 &q, bool all_steps, int *bad_k) -> bool {
+    double prev = 0;
+    for (int k = 0; k < K; ++k) {
+      if (!all_steps && k != 0 && k != K - 1) continue;
+      double t = solve_t(q.Y, q.Z, y0, sR, q.D, q.L0, q.Q0, zp[k], ep[k]);
+      tmin = std::min(tmin, t);
+      tmax = std::max(tmax, t);
+      remmax = std::max(remmax, std::fabs(t - zp[k] - q.Q0));
+      if (all_steps && k > 0) {
+        double st = t - prev;
+        if (!(st > 0)) {
+          *bad_k = k;
+          return false;
+        }
+        minstep = std::min(minstep, st);
+      }
+      prev = t;
+    }
+    return true;
+  };
+  if (P > 0) {
+    int bad_k = -1;
+    if (rows_shared) {
+      for (int i = 0; i < G; ++i)
+        if (!check_group(grp[i], true, &bad_k)) {
+          set_error("dr_plan: depth of row %d not monotone at step %d", i, bad_k);
+          return DR_ERR_NONMONOTONIC;
+        }
+    } else {
+      const int stride = 16;
+      for (int r = 0; r < H; ++r)
+        for (int c = 0; c < W; ++c) {
+          bool sub = (r % stride == 0 || r == H - 1) && (c % stride == 0 || c == W - 1);
+          if (!check_group(grp[(size_t)r * W + c], sub, &bad_k)) {
+            set_error("dr_plan: depth of pixel (%d,%d) not monotone at step %d", r, c, bad_k);
+            return DR_ERR_NONMONOTONIC;
+          }
+        }
+    }
+  }
+  if (P == 0) {
+    tmin = edges[0] * nb;
+    tmax = edges[B] * nb;
+    minstep = 1.0;
+  }
+
+  // ---- fixed-point scale ----
+  double lo = std::min(tmin, edges[0] * nb), hi = std::max(tmax, edges[B] * nb);
+  double origin = 0.5 * (lo + hi);
+  double mag = 0.5 * (hi - lo) * 1.001 + 1e-9;
+  for (int k = 0; k < K; ++k) mag = std::max(mag, std::fabs(zp[k] - origin));
+  for (int i = 0; i < G; ++i) mag = std::max(mag, std::fabs(grp[i].Q0));
+  mag = std::max(mag, remmax * 1.5);
+  int shift = (int)std::floor(std::log2((double)(1 << 29) / mag));
+  shift = std::min(shift, 40);
+  if (shift < 12) {
+    set_error("dr_plan: depth range too large for 32-bit fixed point");
+    return DR_ERR_UNSUPPORTED;
+  }
+  const double scale = std::ldexp(1.0, shift);
+  if (P > 0 && minstep * scale < 64.0) {
+    set_error("dr_plan: depth steps (%.3g mm) too small for the fixed-point grid", minstep);
+    return DR_ERR_UNSUPPORTED;
+  }
+
+  // ---- host tables ----
+  std::vector<GroupC> gc(G);
+  std::vector<GroupD> gd(G);
+  for (int i = 0; i < G; ++i) {
+    const Group64 &q = grp[i];
+    gc[i].Z = (float)q.Z;
+    gc[i].Y2 = (float)(q.Y * q.Y);
+    gc[i].L0 = (float)q.L0;
+    gc[i].invD = (float)(1.0 / q.D);
+    gc[i].D = (float)q.D;
+    gc[i].Q0f = (float)q.Q0;
+    gc[i].Q0fx = (int32_t)std::llround(q.Q0 * scale);
+    gc[i].pad = 0.f;
+    gd[i] = {q.Z, q.Y * q.Y, q.L0, q.D, q.Q0};
+  }
+  std::vector<StepC> sc(K);
+  std::vector<StepD> sd(K);
+  for (int k = 0; k < K; ++k) {
+    sc[k].zf = (float)zp[k];
+    sc[k].eta = (float)ep[k];
+    sc[k].zfx = (int32_t)std::llround((zp[k] - origin) * scale);
+    sc[k].pad = 0.f;
+    sd[k] = {zp[k], ep[k]};
+  }
+  std::vector<int32_t> efx(B + 1);
+  std::vector<double> e64(B + 1);
+  for (int j = 0; j <= B; ++j) {
+    double t = edges[j] * nb - origin;
+    e64[j] = t;
+    double f = std::llround(t * scale);
+    efx[j] = (int32_t)std::max(std::min(f, 2147483000.0), -2147483000.0);
+  }
+
+  // ---- launch shape ----
+  dr_plan_t *p = new (std::nothrow) dr_plan_t();
+  if (!p) {
+    set_error("dr_plan: host allocation failed");
+    return DR_ERR_OOM;
+  }
+  p->rows = H;
+  p->cols = W;
+  p->K = K;
+  p->B = B;
+  p->edge = g->edge;
+  p->kernel = rows_shared ? DR_KERNEL_ROWS : DR_KERNEL_PIXELS;
+  p->out_dtype = opt.out_dtype;
+  p->geom_prec = opt.geom_precision;
+  p->shift = shift;
+  p->nb = nb;
+  p->depth_min = tmin / nb;
+  p->depth_max = tmax / nb;
+  p->min_step = minstep / nb;
+  const bool f64 = opt.geom_precision == DR_GEOM_FP64;
+  Tuning t;
+  choose_chunks(K, &t.kc, &t.nchunks);
+  int Kpad = t.kc * t.nchunks;
+  auto smem_for = [&](int tc) {
+    return rows_shared ? rows_smem_bytes(K, Kpad, B, tc, f64)
+                       : pixels_smem_bytes(K, Kpad, B, tc, f64);
+  };
+  if (rows_shared) {
+    t.ppt = (W % 4 == 0) ? 4 : 1;
+    int tc = opt.tile_cols;
+    if (tc == 0) {
+      tc = 128;
+      int wr = (W + 7) / 8 * 8;
+      if (wr < tc) tc = std::max(wr, 8);
+      // two CTAs per SM when the step count allows it
+      while (tc > 32 && 2 * (smem_for(tc) + 1024) > kSmemPerSm) tc /= 2;
+    }
+    if (tc % 8 != 0 || tc > 256 || tc < 8 || tc % t.ppt != 0) {
+      delete p;
+      set_error("dr_plan: tile_cols must be a multiple of 8 in [8, 256]");
+      return DR_ERR_INVALID_ARG;
+    }
+    t.tile_cols = tc;
+    int lanes = tc / t.ppt;
+    int bg = opt.bin_groups;
+    if (bg == 0) {
+      bg = std::max(1, 128 / lanes);
+      while (bg > 1 && B / bg < 16) bg /= 2;
+      while (lanes * bg > 512) bg /= 2;
+    }
+    if (bg < 1 || lanes * bg > 512) {
+      delete p;
+      set_error("dr_plan: bad bin_groups");
+      return DR_ERR_INVALID_ARG;
+    }
+    t.bin_groups = bg;
+    p->threads = lanes * bg;
+  } else {
+    t.ppt = 1;
+    int tc = opt.tile_cols;
+    if (tc == 0) {
+      tc = 128;
+      int wr = (W + 31) / 32 * 32;
+      if (wr < tc) tc = std::max(wr, 32);
+      while (tc > 32 && 2 * (smem_for(tc) + 1024) > kSmemPerSm) tc /= 2;
+    }
+    if (tc % 32 != 0 || tc > 256) {
+      delete p;
+      set_error("dr_plan: per-pixel tile_cols must be a multiple of 32 up to 256");
+      return DR_ERR_INVALID_ARG;
+    }
+    t.tile_cols = tc;
+    t.bin_groups = 1;
+    p->threads = tc;
+  }
+  p->smem_bytes = smem_for(t.tile_cols);
+  if (p->smem_bytes > kSmemPerCtaMax) {
+    delete p;
+    set_error("dr_plan: %d steps x %d columns do not fit in shared memory", K, t.tile_cols);
+    return DR_ERR_UNSUPPORTED;
+  }
+  p->tune = t;
+
+  // ---- device upload (one allocation) ----
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = align_up(off, 256);
+    off = o + bytes;
+    return o;
+  };
+  size_t o_gc = take(sizeof(GroupC) * G), o_sc = take(sizeof(StepC) * K);
+  size_t o_efx = take(sizeof(int32_t) * (B + 1)), o_gd = take(sizeof(GroupD) * G);
+  size_t o_sd = take(sizeof(StepD) * K), o_e64 = take(sizeof(double) * (B + 1));
+  size_t o_err = take(sizeof(int32_t) * 4);
+  size_t total = align_up(off, 256);
+  void *blk = nullptr;
+  cudaError_t ce = cudaMalloc(&blk, total);
+  if (ce != cudaSuccess) {
+    delete p;
+    if (ce == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      set_error("dr_plan: cudaMalloc of %zu bytes failed", total);
+      return DR_ERR_OOM;
+    }
+    return cuda_fail("dr_plan: cudaMalloc", ce);
+  }
+  std::vector<char> host(total, 0);
+  std::memcpy(host.data() + o_gc, gc.data(), sizeof(GroupC) * G);
+  std::memcpy(host.data() + o_sc, sc.data(), sizeof(StepC) * K);
+  std::memcpy(host.data() + o_efx, efx.data(), sizeof(int32_t) * (B + 1));
+  std::memcpy(host.data() + o_gd, gd.data(), sizeof(GroupD) * G);
+  std::memcpy(host.data() + o_sd, sd.data(), sizeof(StepD) * K);
+  std::memcpy(host.data() + o_e64, e64.data(), sizeof(double) * (B + 1));
+  ce = cudaMemcpy(blk, host.data(), total, cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    cudaFree(blk);
+    delete p;
+    return cuda_fail("dr_plan: upload", ce);
+  }
+  char *b = (char *)blk;
+  p->dev_block = blk;
+  p->device_bytes = total;
+  Consts &c = p->c;
+  c.grp = (const GroupC *)(b + o_gc);
+  c.stp = (const StepC *)(b + o_sc);
+  c.efx = (const int32_t *)(b + o_efx);
+  c.grp64 = (const GroupD *)(b + o_gd);
+  c.stp64 = (const StepD *)(b + o_sd);
+  c.e64 = (const double *)(b + o_e64);
+  c.err = (int32_t *)(b + o_err);
+  c.K = K;
+  c.H = H;
+  c.W = W;
+  c.B = B;
+  c.has_eta = has_eta ? 1 : 0;
+  c.reverse = reverse ? 1 : 0;
+  c.y0 = (float)y0;
+  c.sR = (float)sR;
+  c.scale = (float)scale;
+  c.y0d = y0;
+  c.sRd = sR;
+  c.origin = origin;
+  c.nb = nb;
+  // trailing edge: the reverse change; reversed step order: negated sweep
+  c.out_sign = (float)((g->edge == DR_EDGE_LEADING ? 1.0 : -1.0) * (reverse ? -1.0 : 1.0));
+  *out = p;
+  return DR_OK;
+}
+
+extern "C" void dr_plan_destroy(dr_plan_t *p) {
+  if (!p) return;
+  if (p->dev_block) cudaFree(p->dev_block);
+  delete p;
+}
+
+extern "C" size_t dr_plan_device_bytes(const dr_plan_t *p) { return p ? p->device_bytes : 0; }
+
+extern "C" dr_status dr_plan_get_info(const dr_plan_t *p, dr_plan_info *info) {
+  if (!p || !info) {
+    set_error("dr_plan_get_info: null argument");
+    return DR_ERR_INVALID_ARG;
+  }
+  std::memset(info, 0, sizeof(*info));
+  info->rows = p->rows;
+  info->cols = p->cols;
+  info->K = p->K;
+  info->B = p->B;
+  info->kernel = p->kernel;
+  info->tile_cols = p->tune.tile_cols;
+  info->pixels_per_thread = p->tune.ppt;
+  info->bin_groups = p->tune.bin_groups;
+  info->threads = p->threads;
+  info->smem_bytes = p->smem_bytes;
+  info->tma_chunk = p->tune.kc;
+  info->tma_chunks = p->tune.nchunks;
+  info->out_dtype = p->out_dtype;
+  info->geom_precision = p->geom_prec;
+  info->edge = p->edge;
+  info->reversed = p->c.reverse;
+  info->fixed_shift = p->shift;
+  info->depth_min = p->depth_min;
+  info->depth_max = p->depth_max;
+  info->min_step = p->min_step;
+  info->device_bytes = p->device_bytes;
+  double P = (double)p->rows * p->cols;
+  info->bytes_per_call = 2.0 * P * p->K + (p->out_dtype == DR_OUT_BF16 ? 2.0 : 4.0) * P * p->B;
+  return DR_OK;
+}
+
+extern "C" const char *dr_status_string(dr_status s) {
+  switch (s) {
+    case DR_OK: return "ok";
+    case DR_ERR_INVALID_ARG: return "invalid argument";
+    case DR_ERR_GEOMETRY: return "invalid geometry";
+    case DR_ERR_NONMONOTONIC: return "depth not monotone in the step index";
+    case DR_ERR_OOM: return "out of memory";
+    case DR_ERR_BUDGET: return "over the memory budget";
+    case DR_ERR_CUDA: return "CUDA error";
+    case DR_ERR_TIMEOUT: return "device wait timed out";
+    case DR_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+extern "C" const char *dr_last_error(void) { return g_msg; }
+
+extern "C" const char *dr_version(void) { return "1.0.0"; }

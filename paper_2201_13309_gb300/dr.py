@@ -1,0 +1,251 @@
+"""Python binding of libdr (include/dr.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts Python
+values into the C structs, passes torch tensors' device pointers and CUDA
+stream handles through, and turns status codes into exceptions.  There is no
+fallback: if libdr.so is missing or has no GPU to run on, calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdr.so")
+
+DR_OK = 0
+STATUS = {0: "DR_OK", 1: "DR_ERR_INVALID_ARG", 2: "DR_ERR_GEOMETRY",
+          3: "DR_ERR_NONMONOTONIC", 4: "DR_ERR_OOM", 5: "DR_ERR_BUDGET",
+          6: "DR_ERR_CUDA", 7: "DR_ERR_TIMEOUT", 8: "DR_ERR_UNSUPPORTED"}
+EDGES = {"leading": 0, "trailing": 1}
+OUT_DTYPES = {"f32": 0, "bf16": 1}
+GEOM_PRECISIONS = {"fp32": 0, "fp64": 1}
+KERNELS = {0: "rows", 1: "pixels"}
+
+# every symbol include/dr.h declares (checked by the CPU tests)
+EXPORTS = ("dr_plan", "dr_plan_destroy", "dr_plan_get_info", "dr_plan_device_bytes",
+           "dr_reconstruct", "dr_reconstruct_host", "dr_image_differences",
+           "dr_plan_depths", "dr_plan_check", "dr_status_string", "dr_last_error",
+           "dr_version")
+
+_d3 = ctypes.c_double * 3
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("beam_origin", _d3), ("beam_dir", _d3), ("det_origin", _d3),
+                ("row_step", _d3), ("col_step", _d3), ("rows", ctypes.c_int32),
+                ("cols", ctypes.c_int32), ("wire_axis", _d3),
+                ("wire_radius", ctypes.c_double), ("edge", ctypes.c_int32)]
+
+
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("out_dtype", ctypes.c_int32), ("geom_precision", ctypes.c_int32),
+                ("tile_cols", ctypes.c_int32), ("bin_groups", ctypes.c_int32),
+                ("force_pixels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "rows", "cols", "K", "B", "kernel", "tile_cols", "pixels_per_thread",
+        "bin_groups", "threads", "smem_bytes", "tma_chunk", "tma_chunks", "out_dtype",
+        "geom_precision", "edge", "reversed", "fixed_shift")] + [
+        ("depth_min", ctypes.c_double), ("depth_max", ctypes.c_double),
+        ("min_step", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+        ("bytes_per_call", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {n: getattr(self, n) for n, _ in self._fields_}
+        d["kernel"] = KERNELS.get(d["kernel"], d["kernel"])
+        return d
+
+
+class DrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libdr.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            P, I32, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+            sig = {
+                "dr_plan": ([ctypes.POINTER(Geometry), P, I32, P, I32,
+                             ctypes.POINTER(PlanOptions), ctypes.POINTER(P)], I32),
+                "dr_plan_destroy": ([P], None),
+                "dr_plan_get_info": ([P, ctypes.POINTER(PlanInfo)], I32),
+                "dr_plan_device_bytes": ([P], SZ),
+                "dr_reconstruct": ([P, P, P, P], I32),
+                "dr_reconstruct_host": ([P, P, P, P, P, P], I32),
+                "dr_image_differences": ([P, I32, I32, I32, P, P], I32),
+                "dr_plan_depths": ([P, I32, I32, P, P], I32),
+                "dr_plan_check": ([P], I32),
+                "dr_status_string": ([I32], ctypes.c_char_p),
+                "dr_last_error": ([], ctypes.c_char_p),
+                "dr_version": ([], ctypes.c_char_p),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def check(status):
+    if status != DR_OK:
+        raise DrError(status, lib().dr_last_error().decode())
+
+
+def geometry_struct(geom, edge="leading"):
+    g = Geometry()
+    for key in ("beam_origin", "beam_dir", "det_origin", "row_step", "col_step",
+                "wire_axis"):
+        setattr(g, key, _d3(*[float(v) for v in geom[key]]))
+    g.rows = int(geom["rows"])
+    g.cols = int(geom["cols"])
+    g.wire_radius = float(geom["wire_radius"])
+    g.edge = EDGES[edge] if isinstance(edge, str) else int(edge)
+    return g
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A reconstruction plan (dr_plan): geometry, wire path and bin edges.
+
+    geom: dict with beam_origin, beam_dir, det_origin, row_step, col_step,
+    rows, cols, wire_axis, wire_radius (mm); wires [K, 3]; edges [B + 1]
+    (depth, mm, strictly increasing).
+    """
+
+    def __init__(self, geom, wires, edges, edge="leading", out_dtype="f32",
+                 geom_precision="fp32", tile_cols=0, bin_groups=0, force_pixels=False):
+        L = lib()
+        self._wires = np.ascontiguousarray(wires, dtype=np.float64)
+        self._edges = np.ascontiguousarray(edges, dtype=np.float64)
+        self.geom = dict(geom)
+        self.edge = edge
+        self.out_dtype = out_dtype
+        g = geometry_struct(geom, edge)
+        o = PlanOptions()
+        o.out_dtype = OUT_DTYPES[out_dtype]
+        o.geom_precision = GEOM_PRECISIONS[geom_precision]
+        o.tile_cols = int(tile_cols)
+        o.bin_groups = int(bin_groups)
+        o.force_pixels = 1 if force_pixels else 0
+        h = ctypes.c_void_p()
+        check(L.dr_plan(ctypes.byref(g), self._wires.ctypes.data_as(ctypes.c_void_p),
+                        self._wires.shape[0], self._edges.ctypes.data_as(ctypes.c_void_p),
+                        self._edges.shape[0] - 1, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.K = int(self._wires.shape[0])
+        self.B = int(self._edges.shape[0] - 1)
+        self.rows = int(geom["rows"])
+        self.cols = int(geom["cols"])
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        i = PlanInfo()
+        check(lib().dr_plan_get_info(self._h, ctypes.byref(i)))
+        return i.as_dict()
+
+    def out_torch_dtype(self):
+        import torch
+        return torch.bfloat16 if self.out_dtype == "bf16" else torch.float32
+
+    def empty_output(self, device="cuda"):
+        import torch
+        return torch.empty((self.B, self.rows, self.cols), dtype=self.out_torch_dtype(),
+                           device=device)
+
+    def reconstruct(self, images, out=None, stream=None):
+        """images: CUDA tensor [K, rows, cols] of uint16 bits (int16 or uint16
+        dtype); out: CUDA tensor [B, rows, cols] (allocated if None)."""
+        if out is None:
+            out = self.empty_output(images.device)
+        self._check_shapes(images, out)
+        check(lib().dr_reconstruct(self._h, _dptr(images), _dptr(out),
+                                   ctypes.c_void_p(_stream_handle(stream))))
+        return out
+
+    def reconstruct_host(self, h_images, h_out, d_images, d_out, stream=None):
+        """End to end: pinned host images -> device -> reconstruct -> host."""
+        self._check_shapes(d_images, d_out)
+        check(lib().dr_reconstruct_host(self._h, _dptr(h_images), _dptr(h_out),
+                                        _dptr(d_images), _dptr(d_out),
+                                        ctypes.c_void_p(_stream_handle(stream))))
+        return h_out
+
+    def depths(self, r0=0, nrows=None, stream=None):
+        """The GPU's depths d_k (mm) for rows r0..: CUDA float64 [nrows, cols, K]."""
+        import torch
+        nrows = self.rows - r0 if nrows is None else nrows
+        d = torch.empty((nrows, self.cols, self.K), dtype=torch.float64, device="cuda")
+        check(lib().dr_plan_depths(self._h, r0, nrows, _dptr(d),
+                                   ctypes.c_void_p(_stream_handle(stream))))
+        return d
+
+    def check_device(self):
+        check(lib().dr_plan_check(self._h))
+
+    def _check_shapes(self, images, out):
+        if tuple(images.shape) != (self.K, self.rows, self.cols):
+            raise ValueError(f"images {tuple(images.shape)} != {(self.K, self.rows, self.cols)}")
+        if tuple(out.shape) != (self.B, self.rows, self.cols):
+            raise ValueError(f"out {tuple(out.shape)} != {(self.B, self.rows, self.cols)}")
+        if images.element_size() != 2 or not images.is_contiguous() or not out.is_contiguous():
+            raise ValueError("images must be contiguous 16-bit, out contiguous")
+        if out.dtype != self.out_torch_dtype():
+            raise ValueError(f"out dtype {out.dtype} != {self.out_torch_dtype()}")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().dr_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def image_differences(images, stream=None):
+    """int32 [K-1, rows, cols]: exact I_k - I_{k+1} as the kernels form it."""
+    import torch
+    K, H, W = images.shape
+    d = torch.empty((max(K - 1, 0), H, W), dtype=torch.int32, device=images.device)
+    check(lib().dr_image_differences(_dptr(images), K, H, W, _dptr(d),
+                                     ctypes.c_void_p(_stream_handle(stream))))
+    return d
+
+
+def version():
+    return lib().dr_version().decode()

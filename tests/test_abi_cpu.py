@@ -1,0 +1,82 @@
+"""The C ABI library loads, exports every declared symbol, and validates its
+inputs on the host (no GPU needed: every case fails before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2201_13309_gb300 import _build, dr, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return dr.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "dr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dr_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declarations_match_binding():
+    assert set(declared_symbols()) == set(dr.EXPORTS)
+
+
+def test_library_exports_every_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    assert dr.version() == "1.0.0"
+    assert lib.dr_status_string(3).decode().startswith("depth not monotone")
+
+
+def _plan_status(geom, wires, edges, edge="leading"):
+    L = dr.lib()
+    g = dr.geometry_struct(geom, edge)
+    w = np.ascontiguousarray(wires, dtype=np.float64)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    h = ctypes.c_void_p()
+    st = L.dr_plan(ctypes.byref(g), w.ctypes.data_as(ctypes.c_void_p), w.shape[0],
+                   e.ctypes.data_as(ctypes.c_void_p), e.shape[0] - 1, None,
+                   ctypes.byref(h))
+    assert not h.value
+    return st, L.dr_last_error().decode()
+
+
+def test_plan_rejects_bad_inputs(lib):
+    g = synth.detector_geometry(8, 8)
+    w = synth.wire_path(5)
+    e = synth.bin_edges(-10, 10, 1.0)
+    assert _plan_status(g, w[:1], e)[0] == 1                     # K < 2
+    assert _plan_status(g, w, e[:1])[0] == 1                     # B < 1
+    bad = e.copy()
+    bad[3] = bad[2]
+    assert _plan_status(g, w, bad)[0] == 1                       # not increasing
+    g2 = dict(g, beam_dir=[1.0, 0.0, 0.0])
+    assert _plan_status(g2, w, e)[0] == 2                        # beam along wire
+    still = np.repeat(w[:1], 5, axis=0)
+    assert _plan_status(g, still, e)[0] == 2                     # no travel
+    low = w.copy()
+    low[:, 1] = 0.01
+    assert _plan_status(g, low, e)[0] == 2                       # wire hits beam
+    far = w.copy()
+    far[:, 1] = 600.0
+    assert _plan_status(g, far, e)[0] == 2                       # wire past detector
+    zig = w.copy()
+    zig[2, 2] = zig[0, 2] - 0.003
+    st, msg = _plan_status(g, zig, e)
+    assert st == 3 and "monotone" in msg                         # depth goes back
+    g3 = dict(g, rows=-1)
+    assert _plan_status(g3, w, e)[0] == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(dr, "LIB_PATH", str(tmp_path / "libdr.so"))
+    monkeypatch.setattr(dr, "_lib", None)
+    with pytest.raises(ImportError):
+        dr.lib()
