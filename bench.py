@@ -24,7 +24,6 @@ import argparse
 import ctypes
 import hashlib
 import json
-import math
 import os
 import statistics
 import sys
@@ -243,6 +242,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--tile-cols", type=int, default=0, help="fixed tile width (0: autotune)")
+    ap.add_argument("--bin-groups", type=int, default=0)
+    ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--rows", type=int, default=2048,
                     help="reconstruct only the first ROWS detector rows (small profiling case)")
     args = ap.parse_args()
@@ -278,9 +280,18 @@ def main():
                                      spec.scat.spot_row[keep], spec.scat.spot_col[keep])
     images = synth.device_spot_images(spec.geom, spec.wires, spec.scat, seed=rank, background=20.0,
                                       device=dev)
-    plan = dr.Plan(spec.geom, spec.wires, spec.edges)
+    from paper_2201_13309_gb300 import autotune
+
+    out = torch.empty((spec.B, spec.geom["rows"], spec.geom["cols"]), dtype=torch.float32,
+                      device=dev)
+    if args.tile_cols:
+        plan = dr.Plan(spec.geom, spec.wires, spec.edges, tile_cols=args.tile_cols,
+                       bin_groups=args.bin_groups)
+        tuned = None
+    else:
+        plan, tuned = autotune.tuned_plan(spec.geom, spec.wires, spec.edges, images, out=out,
+                                          use_cache=not args.retune)
     info = plan.info()
-    out = plan.empty_output(dev)
     stream = torch.cuda.Stream(dev)
     P = spec.P
     units_per_step = P * spec.K
@@ -390,7 +401,11 @@ def main():
                        "kernel": info["kernel"], "tile_cols": info["tile_cols"],
                        "pixels_per_thread": info["pixels_per_thread"],
                        "bin_groups": info["bin_groups"], "threads": info["threads"],
-                       "smem_bytes": info["smem_bytes"]},
+                       "smem_bytes": info["smem_bytes"],
+                       "autotuned": None if tuned is None else {
+                           "cached": tuned["cached"],
+                           "candidates_ms": {f"{c['tile_cols']}x{c['bin_groups']}": round(c["ms"], 4)
+                                             for c in tuned.get("candidates", [])}}},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

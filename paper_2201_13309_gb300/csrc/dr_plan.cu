@@ -94,19 +94,31 @@ int pixels_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64) {
   return (int)s;
 }
 
-void choose_chunks(int K, int *kc, int *nchunks) {
+// TMA chunks of kc steps: at most 256 steps per box, and every chunk's
+// shared-memory destination (kc * tile_cols * 2 bytes apart) 128-byte aligned,
+// as tensor copies require.  Picks the chunk count with the least padding.
+void choose_chunks(int K, int tile_cols, int *kc, int *nchunks) {
+  int g = 64, x = tile_cols;
+  while (x % 2 == 0 && g > 1) {
+    x /= 2;
+    g /= 2;
+  }
+  const int m = g;  // kc must be a multiple of m = 64 / gcd(tile_cols, 64)
   int nmin = (K + 255) / 256;
-  int best_n = nmin, best_pad = 1 << 30;
+  int best_n = nmin, best_c = 0, best_pad = 1 << 30;
   for (int n = nmin; n <= nmin + 4; ++n) {
     int c = (K + n - 1) / n;
+    c = (c + m - 1) / m * m;
+    if (c > 256) continue;
     int pad = n * c - K;
     if (pad < best_pad) {
       best_pad = pad;
       best_n = n;
+      best_c = c;
     }
   }
   *nchunks = best_n;
-  *kc = (K + best_n - 1) / best_n;
+  *kc = best_c;
 }
 
 constexpr int kSmemPerSm = 228 * 1024;
@@ -384,11 +396,11 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires,
   p->min_step = minstep / nb;
   const bool f64 = opt.geom_precision == DR_GEOM_FP64;
   Tuning t;
-  choose_chunks(K, &t.kc, &t.nchunks);
-  int Kpad = t.kc * t.nchunks;
   auto smem_for = [&](int tc) {
-    return rows_shared ? rows_smem_bytes(K, Kpad, B, tc, f64)
-                       : pixels_smem_bytes(K, Kpad, B, tc, f64);
+    int kc, n;
+    choose_chunks(K, tc, &kc, &n);
+    return rows_shared ? rows_smem_bytes(K, kc * n, B, tc, f64)
+                       : pixels_smem_bytes(K, kc * n, B, tc, f64);
   };
   if (rows_shared) {
     t.ppt = (W % 4 == 0) ? 4 : 1;
@@ -409,7 +421,7 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires,
     int lanes = tc / t.ppt;
     int bg = opt.bin_groups;
     if (bg == 0) {
-      bg = std::max(1, 128 / lanes);
+      bg = std::max(1, 512 / lanes);
       while (bg > 1 && B / bg < 16) bg /= 2;
       while (lanes * bg > 512) bg /= 2;
     }
@@ -437,6 +449,12 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires,
     t.tile_cols = tc;
     t.bin_groups = 1;
     p->threads = tc;
+  }
+  choose_chunks(K, t.tile_cols, &t.kc, &t.nchunks);
+  if (t.kc < 1 || t.kc > 256 || ((size_t)t.kc * t.tile_cols * 2) % 128 != 0) {
+    delete p;
+    set_error("dr_plan: no aligned TMA chunking for K=%d, tile_cols=%d", K, t.tile_cols);
+    return DR_ERR_UNSUPPORTED;
   }
   p->smem_bytes = smem_for(t.tile_cols);
   if (p->smem_bytes > kSmemPerCtaMax) {

@@ -301,13 +301,19 @@ __global__ void __launch_bounds__(512) rows_kernel(const __grid_constant__ CUten
 
   stage_tile<kTma>(&tmap, img, simg, bar, c, t, row, c0);
 
+  int *zcount = reinterpret_cast<int *>(bar + 1);
+  if (tid == 0) zcount[0] = zcount[1] = 0;
   // depth positions of this row (processing order: increasing depth)
   const auto &g = Geo::group(c, row);
   const auto *steps = Geo::steps(c);
   for (int k = tid; k < K; k += NT) spos[k] = Geo::depth(g, steps[k], c);
   __syncthreads();
   // each bin edge -> (k, f): k = last step below the edge (clamped to an
-  // interval), f = position of the edge inside [d_k, d_{k+1}], clamped
+  // interval), f = position of the edge inside [d_k, d_{k+1}], clamped.
+  // Edges at or below d_0 give F = 0 and edges at or above d_{K-1} give
+  // F = S_{K-1}, so only bins [nz_lo, nz_hi) can hold data.
+  int below = 0, above = 0;
+  const pos_t tfirst = spos[0], tlast = spos[K - 1];
   for (int j = tid; j <= B; j += NT) {
     const pos_t e = Geo::edge(c, j);
     int lo = 0, hi = K;
@@ -318,55 +324,69 @@ __global__ void __launch_bounds__(512) rows_kernel(const __grid_constant__ CUten
     const int k = min(max(lo - 1, 0), K - 2);
     const float f = Geo::frac(e, spos[k], Geo::inv_len(spos[k], spos[k + 1]));
     stab[j] = make_int2(k, __float_as_int(f));
+    below += !(e > tfirst);
+    above += !(e < tlast);
   }
+  if (below) atomicAdd(&zcount[0], below);
+  if (above) atomicAdd(&zcount[1], above);
   __syncthreads();
+  const int nz_hi = min(B + 1 - zcount[1], B);
+  const int nz_lo = min(max(zcount[0] - 1, 0), nz_hi);
   if constexpr (kTma) {
     if (!mbar_wait_bounded(bar, 0, c.err)) return;
   }
 
-  // stream the bins; thread = PPT adjacent pixels x one contiguous bin range
+  // stream the bins; thread = PPT adjacent pixels; the zero ranges and the
+  // data range are each split evenly over the bin groups
   const int lanes = TC / PPT;
   const int lane = tid % lanes, grp = tid / lanes;
   const int lc = lane * PPT, col = c0 + lc;
   if (col >= c.W) return;
-  const int jb = (int)((long long)B * grp / t.bin_groups);
-  const int je = (int)((long long)B * (grp + 1) / t.bin_groups);
-  if (jb >= je) return;
+  const int G = t.bin_groups;
+  auto slice_lo = [&](int lo, int hi) { return lo + (int)((long long)(hi - lo) * grp / G); };
+  auto slice_hi = [&](int lo, int hi) { return lo + (int)((long long)(hi - lo) * (grp + 1) / G); };
+  const float sign = c.out_sign;
+  const size_t plane = (size_t)c.H * c.W;
+  OutT *const o0 = out + (size_t)row * c.W + col;
+  float zero[PPT];
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) zero[i] = __fmul_rn(sign, 0.f);
+  auto zero_fill = [&](int a, int b) {
+    OutT *o = o0 + (size_t)a * plane;
+#pragma unroll 4
+    for (int j = a; j < b; ++j, o += plane) store_px<OutT, PPT>(o, zero);
+  };
+  zero_fill(slice_lo(0, nz_lo), slice_hi(0, nz_lo));
+  zero_fill(slice_lo(nz_hi, B), slice_hi(nz_hi, B));
+
+  const int a = slice_lo(nz_lo, nz_hi), b = slice_hi(nz_lo, nz_hi);
+  if (a >= b) return;
   const bool rev = c.reverse != 0;
   auto srow = [&](int k) { return simg + (size_t)(rev ? K - 1 - k : k) * TC + lc; };
   float I0[PPT];
   load_px<PPT>(srow(0), I0);
   auto evalF = [&](int2 kf, float (&F)[PPT]) {
-    float a[PPT], b[PPT];
-    load_px<PPT>(srow(kf.x), a);
-    load_px<PPT>(srow(kf.x + 1), b);
+    float x[PPT], y[PPT];
+    load_px<PPT>(srow(kf.x), x);
+    load_px<PPT>(srow(kf.x + 1), y);
     const float f = __int_as_float(kf.y);
 #pragma unroll
     for (int i = 0; i < PPT; ++i)
-      F[i] = __fmaf_rn(f, __fsub_rn(a[i], b[i]), __fsub_rn(I0[i], a[i]));
+      F[i] = __fmaf_rn(f, __fsub_rn(x[i], y[i]), __fsub_rn(I0[i], x[i]));
   };
-  const float sign = c.out_sign;
-  const size_t plane = (size_t)c.H * c.W;
-  OutT *o = out + (size_t)jb * plane + (size_t)row * c.W + col;
-  int2 tp = stab[jb];
   float Fp[PPT];
-  evalF(tp, Fp);
-  for (int j = jb; j < je; ++j, o += plane) {
-    const int2 tn = stab[j + 1];
+  evalF(stab[a], Fp);
+  OutT *o = o0 + (size_t)a * plane;
+#pragma unroll 4
+  for (int j = a; j < b; ++j, o += plane) {
     float Fn[PPT], v[PPT];
-    if (tn.x == tp.x && tn.y == tp.y) {
-#pragma unroll
-      for (int i = 0; i < PPT; ++i) Fn[i] = Fp[i];
-    } else {
-      evalF(tn, Fn);
-    }
+    evalF(stab[j + 1], Fn);
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
       v[i] = __fmul_rn(sign, __fsub_rn(Fn[i], Fp[i]));
       Fp[i] = Fn[i];
     }
     store_px<OutT, PPT>(o, v);
-    tp = tn;
   }
 }
 

@@ -281,7 +281,7 @@ def spot_contributions(geom, wires, scat, spot_sigma=1.0):
 
 
 def device_spot_images(geom, wires, scat, seed, background, device,
-                       step_chunk=16):
+                       step_chunk=64):
     """Poisson spot-scan image stack built on a CUDA device.
 
     Returns a torch int16 tensor [K, rows, cols] holding the uint16 bit

@@ -126,6 +126,35 @@ def test_tile_overrides_agree_bitwise():
         assert torch.equal(a.view(torch.int32), b.view(torch.int32)), (tc, bg)
 
 
+@pytest.mark.parametrize("tc", [8, 16, 32, 40, 64])
+def test_small_tiles_multi_chunk(tc):
+    """More than one TMA chunk of steps with narrow tiles (the chunk stride in
+    shared memory must stay 128-byte aligned)."""
+    sc = synth.tiny_scan(13, rows=3, cols=160, K=301, n_scat=3)
+    sc.edges = synth.bin_edges(-40, 340, 2.0)
+    _, a = run(sc)
+    plan, b = run(sc, tile_cols=tc, bin_groups=2)
+    info = plan.info()
+    assert info["tma_chunks"] >= 2 and (info["tma_chunk"] * tc * 2) % 128 == 0
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+    assert_parity(b.cpu().numpy(), ref_of(sc), sc.images)
+
+
+def test_autotuner_picks_a_valid_shape(tmp_path, monkeypatch):
+    from paper_2201_13309_gb300 import autotune
+
+    monkeypatch.setenv("DR_TUNE_CACHE", str(tmp_path / "tune.json"))
+    sc = synth.tiny_scan(14, rows=8, cols=256, K=41)
+    img = to_dev(sc.images)
+    plan, best = autotune.tuned_plan(sc.geom, sc.wires, sc.edges, img, reps=2)
+    assert not best["cached"] and len(best["candidates"]) >= 3
+    out = plan.reconstruct(img)
+    torch.cuda.synchronize()
+    assert_parity(out.cpu().numpy(), ref_of(sc), sc.images)
+    again = autotune.tune(sc.geom, sc.wires, sc.edges, img)
+    assert again["cached"] and again["tile_cols"] == best["tile_cols"]
+
+
 def test_fp64_geometry_variant():
     sc = synth.tiny_scan(7)
     _, out = run(sc, geom_precision="fp64")
