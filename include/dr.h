@@ -162,6 +162,42 @@ dr_status dr_plan_depths(const dr_plan_t *plan, int32_t r0, int32_t nrows,
  * wait ran out).  Synchronizes the device.  DR_OK or DR_ERR_TIMEOUT. */
 dr_status dr_plan_check(const dr_plan_t *plan);
 
+/* ---- Reconstruction that allocates nothing -------------------------------
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot call cudaMalloc themselves and so cannot build a plan (dr_plan keeps
+ * its tables in device memory it allocates): for example a program whose
+ * device memory is all handed out by another allocator (a framework's caching
+ * pool that reserves the GPU), or an acquisition pipeline that forbids device
+ * allocation once running because cudaMalloc/cudaFree may block or
+ * synchronize the device.
+ *
+ * It runs the same rows kernel as dr_reconstruct for detectors whose columns
+ * run along the wire axis, FP32 geometry and FP32 output.  Its geometry
+ * tables (per-row constants, per-step constants, fixed-point bin edges and an
+ * error word) live in one file-scope device array of 2 MiB
+ * (DR_STATIC_SCRATCH_BYTES) inside the library; every GPU that loads the
+ * library holds that array until the process exits.  The tables of a call
+ * need 32*rows + 16*K + 4*(B+1) bytes plus alignment (at most 2 MiB, and
+ * K <= 16384); larger requests return DR_ERR_BUDGET, detectors whose columns
+ * do not run along the wire axis DR_ERR_UNSUPPORTED.  Arguments are those of
+ * dr_plan + dr_reconstruct; d_status is an optional device int32 that is
+ * cleared and then receives a device-side error code (nonzero: a bounded wait
+ * ran out); with d_status null the code stays in the library's array.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Each call copies its tables into the array on
+ * stream (the host side is serialised by a lock), so every call shares the
+ * array and leaves its own tables there: calls on one stream are ordered,
+ * but calls whose work overlaps on the GPU (other streams, other threads)
+ * race on the array and must not be issued. */
+#define DR_STATIC_SCRATCH_BYTES (2u << 20)
+dr_status dr_reconstruct_rows_static(const dr_geometry *geometry,
+                                     const double *wire_centres, int32_t K,
+                                     const double *bin_edges, int32_t B,
+                                     const uint16_t *d_images, float *d_out,
+                                     int32_t *d_status, dr_stream_t stream);
+
 const char *dr_status_string(dr_status status);
 /* One line describing the last failure on the calling thread ("" if none). */
 const char *dr_last_error(void);

@@ -102,6 +102,24 @@ struct dr_plan {
 };
 
 namespace dr {
+
+// Layout of the rows-kernel tables when they are built into a fixed buffer
+// instead of a plan's own device allocation (offsets from the buffer start).
+struct StaticTables {
+  size_t off_grp, off_stp, off_efx, off_err, bytes;
+  Consts c;                // pointers hold offsets until rebased
+  Tuning tune;
+  int rows, cols, K, B, threads, smem_bytes;
+};
+
+// Builds GroupC[rows] / StepC[K] / fixed-point edges / a zeroed error word
+// into stage (cap bytes), using tmp (2*K doubles) as host scratch.  Only for
+// detectors whose columns run along the wire axis (the rows kernel), FP32
+// geometry; DR_ERR_BUDGET when the tables exceed cap.
+dr_status build_rows_tables(const dr_geometry *g, const double *wires, int K,
+                            const double *edges, int B, unsigned char *stage, size_t cap,
+                            double *tmp, StaticTables *out);
+
 void set_error(const char *fmt, ...);
 dr_status cuda_fail(const char *what, int err);
 }  // namespace dr

@@ -588,3 +588,220 @@ extern "C" const char *dr_status_string(dr_status s) {
 extern "C" const char *dr_last_error(void) { return g_msg; }
 
 extern "C" const char *dr_version(void) { return "1.0.0"; }
+
+// ---------------------------------------------------------------------------
+// Rows-kernel tables built into a fixed buffer (no allocation of any kind):
+// the same FP64 frame, per-row constants, monotonicity check and fixed-point
+// scale as dr_plan, restricted to detectors whose columns run along the wire
+// axis and to FP32 geometry.
+dr_status dr::build_rows_tables(const dr_geometry *g, const double *wires, int K,
+                                const double *edges, int B, unsigned char *stage, size_t cap,
+                                double *tmp, StaticTables *out) {
+  if (!g || !wires || !edges || !stage || !tmp || !out) {
+    set_error("null argument");
+    return DR_ERR_INVALID_ARG;
+  }
+  if (K < 2 || B < 1 || g->rows < 0 || g->cols < 0 || g->rows > 65535 ||
+      (g->edge != DR_EDGE_LEADING && g->edge != DR_EDGE_TRAILING)) {
+    set_error("need K >= 2, B >= 1, 0 <= rows <= 65535, cols >= 0, a valid edge");
+    return DR_ERR_INVALID_ARG;
+  }
+  for (int j = 0; j <= B; ++j)
+    if (!std::isfinite(edges[j]) || (j > 0 && !(edges[j] > edges[j - 1]))) {
+      set_error("bin edges must be finite and strictly increasing (j=%d)", j);
+      return DR_ERR_INVALID_ARG;
+    }
+  for (int k = 0; k < K; ++k)
+    if (!finite3(wires + 3 * k)) {
+      set_error("wire centre %d not finite", k);
+      return DR_ERR_INVALID_ARG;
+    }
+  if (!finite3(g->beam_origin) || !finite3(g->beam_dir) || !finite3(g->det_origin) ||
+      !finite3(g->row_step) || !finite3(g->col_step) || !finite3(g->wire_axis) ||
+      !std::isfinite(g->wire_radius) || !(g->wire_radius > 0.0)) {
+    set_error("geometry not finite or radius <= 0");
+    return DR_ERR_INVALID_ARG;
+  }
+  const int H = g->rows, W = g->cols;
+  const size_t o_grp = 0;
+  const size_t o_stp = align_up(o_grp + sizeof(GroupC) * (size_t)H, 256);
+  const size_t o_efx = align_up(o_stp + sizeof(StepC) * (size_t)K, 256);
+  const size_t o_err = align_up(o_efx + sizeof(int32_t) * (size_t)(B + 1), 256);
+  const size_t bytes = o_err + 256;
+  if (bytes > cap) {
+    set_error("tables need %zu bytes of static scratch; the limit is %zu", bytes, cap);
+    return DR_ERR_BUDGET;
+  }
+  V3 ax = v3(g->wire_axis), bd = v3(g->beam_dir), O = v3(g->beam_origin);
+  if (!(norm(ax) > 0) || !(norm(bd) > 0)) {
+    set_error("zero wire axis or beam direction");
+    return DR_ERR_GEOMETRY;
+  }
+  ax = (1.0 / norm(ax)) * ax;
+  bd = (1.0 / norm(bd)) * bd;
+  const V3 bp = bd - dot(bd, ax) * ax;
+  const double nb = norm(bp);
+  if (!(nb > 1e-9)) {
+    set_error("beam runs along the wire axis");
+    return DR_ERR_GEOMETRY;
+  }
+  const V3 e2 = (1.0 / nb) * bp;
+  V3 w = v3(wires) - O;
+  w = w - dot(w, ax) * ax;
+  w = w - dot(w, e2) * e2;
+  if (!(norm(w) > 0)) {
+    set_error("first wire centre lies on the beam");
+    return DR_ERR_GEOMETRY;
+  }
+  const V3 e1 = (1.0 / norm(w)) * w;
+  const double R = g->wire_radius;
+  double *zp = tmp, *ep = tmp + K;
+  const double z_first = dot(v3(wires) - O, e2);
+  const double z_last = dot(v3(wires + 3 * (K - 1)) - O, e2);
+  if (z_last == z_first) {
+    set_error("wire does not travel along the projected beam");
+    return DR_ERR_GEOMETRY;
+  }
+  const bool reverse = z_last < z_first;
+  const double y_first = dot(v3(wires) - O, e1);
+  double ymin = 1e300, ymax = -1e300;
+  bool has_eta = false;
+  for (int k = 0; k < K; ++k) {  // processing order: increasing depth
+    const V3 c = v3(wires + 3 * (reverse ? K - 1 - k : k)) - O;
+    zp[k] = dot(c, e2);
+    const double yk = dot(c, e1);
+    ep[k] = yk - y_first;
+    has_eta |= (yk != y_first);
+    ymin = std::min(ymin, yk);
+    ymax = std::max(ymax, yk);
+  }
+  if (!(ymin > R)) {
+    set_error("wire overlaps the beam");
+    return DR_ERR_GEOMETRY;
+  }
+  const double sR = (reverse ? -1.0 : 1.0) * (g->edge == DR_EDGE_LEADING ? 1.0 : -1.0) * R;
+  const V3 dorg = v3(g->det_origin) - O, rs = v3(g->row_step), cs = v3(g->col_step);
+  const double Y00 = dot(dorg, e1), Z00 = dot(dorg, e2), Yr = dot(rs, e1), Zr = dot(rs, e2);
+  if (std::fabs(dot(cs, e1)) + std::fabs(dot(cs, e2)) > 1e-13 * std::max(norm(cs), 1e-300)) {
+    set_error("detector columns must run along the wire axis for this entry point");
+    return DR_ERR_UNSUPPORTED;
+  }
+  if (H > 0 && W > 0 && !(std::min(Y00, Y00 + (H - 1) * Yr) - ymax > R)) {
+    set_error("wire not between beam and detector");
+    return DR_ERR_GEOMETRY;
+  }
+  // per-row constants (FP64), depth range and monotonicity
+  double tmin = edges[0] * nb, tmax = edges[B] * nb, minstep = 1e300, remmax = 0.0,
+         qmax = 0.0;
+  for (int r = 0; r < H && W > 0; ++r) {
+    const double Y = Y00 + r * Yr, Z = Z00 + r * Zr, D = Y - y_first;
+    const double L0 = std::sqrt(Y * Y + Z * Z), Q0 = (-y_first * Z + sR * L0) / D;
+    qmax = std::max(qmax, std::fabs(Q0));
+    double prev = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const double t = solve_t(Y, Z, y_first, sR, D, L0, Q0, zp[k], ep[k]);
+      tmin = std::min(tmin, t);
+      tmax = std::max(tmax, t);
+      remmax = std::max(remmax, std::fabs(t - zp[k] - Q0));
+      if (k > 0) {
+        if (!(t - prev > 0)) {
+          set_error("depth of row %d not monotone at step %d", r, k);
+          return DR_ERR_NONMONOTONIC;
+        }
+        minstep = std::min(minstep, t - prev);
+      }
+      prev = t;
+    }
+  }
+  const double origin = 0.5 * (tmin + tmax);
+  double mag = std::max(0.5 * (tmax - tmin) * 1.001 + 1e-9, std::max(qmax, remmax * 1.5));
+  for (int k = 0; k < K; ++k) mag = std::max(mag, std::fabs(zp[k] - origin));
+  int shift = std::min((int)std::floor(std::log2((double)(1 << 29) / mag)), 40);
+  if (shift < 12) {
+    set_error("depth range too large for 32-bit fixed point");
+    return DR_ERR_UNSUPPORTED;
+  }
+  const double scale = std::ldexp(1.0, shift);
+  if (H > 0 && W > 0 && minstep * scale < 64.0) {
+    set_error("depth steps too small for the fixed-point grid");
+    return DR_ERR_UNSUPPORTED;
+  }
+  // launch shape: the dr_plan defaults
+  Tuning t;
+  t.ppt = (W % 4 == 0) ? 4 : 1;
+  int tc = std::min(128, std::max((W + 7) / 8 * 8, 8));
+  int kc, n;
+  auto smem_for = [&](int c) {
+    choose_chunks(K, c, &kc, &n);
+    return rows_smem_bytes(K, kc * n, B, c, false);
+  };
+  while (tc > 32 && 2 * (smem_for(tc) + 1024) > kSmemPerSm) tc /= 2;
+  const int smem = smem_for(tc);
+  if (smem > kSmemPerCtaMax || kc < 1 || ((size_t)kc * tc * 2) % 128 != 0) {
+    set_error("%d steps do not fit in shared memory", K);
+    return DR_ERR_UNSUPPORTED;
+  }
+  t.tile_cols = tc;
+  t.kc = kc;
+  t.nchunks = n;
+  const int lanes = tc / t.ppt;
+  int bg = std::max(1, 512 / lanes);
+  while (bg > 1 && B / bg < 16) bg /= 2;
+  while (lanes * bg > 512) bg /= 2;
+  t.bin_groups = bg;
+  // tables
+  std::memset(stage, 0, bytes);
+  GroupC *gc = reinterpret_cast<GroupC *>(stage + o_grp);
+  for (int r = 0; r < H; ++r) {
+    const double Y = Y00 + r * Yr, Z = Z00 + r * Zr, D = Y - y_first;
+    const double L0 = std::sqrt(Y * Y + Z * Z), Q0 = (-y_first * Z + sR * L0) / D;
+    gc[r].Z = (float)Z;
+    gc[r].Y2 = (float)(Y * Y);
+    gc[r].L0 = (float)L0;
+    gc[r].invD = (float)(1.0 / D);
+    gc[r].D = (float)D;
+    gc[r].Q0f = (float)Q0;
+    gc[r].Q0fx = (int32_t)std::llround(Q0 * scale);
+  }
+  StepC *sc = reinterpret_cast<StepC *>(stage + o_stp);
+  for (int k = 0; k < K; ++k) {
+    sc[k].zf = (float)zp[k];
+    sc[k].eta = (float)ep[k];
+    sc[k].zfx = (int32_t)std::llround((zp[k] - origin) * scale);
+  }
+  int32_t *efx = reinterpret_cast<int32_t *>(stage + o_efx);
+  for (int j = 0; j <= B; ++j) {
+    const double f = (double)std::llround((edges[j] * nb - origin) * scale);
+    efx[j] = (int32_t)std::max(std::min(f, 2147483000.0), -2147483000.0);
+  }
+  StaticTables &st = *out;
+  std::memset(&st, 0, sizeof(st));
+  st.off_grp = o_grp;
+  st.off_stp = o_stp;
+  st.off_efx = o_efx;
+  st.off_err = o_err;
+  st.bytes = bytes;
+  st.tune = t;
+  st.rows = H;
+  st.cols = W;
+  st.K = K;
+  st.B = B;
+  st.threads = lanes * bg;
+  st.smem_bytes = smem;
+  Consts &c = st.c;
+  c.K = K;
+  c.H = H;
+  c.W = W;
+  c.B = B;
+  c.has_eta = has_eta ? 1 : 0;
+  c.reverse = reverse ? 1 : 0;
+  c.y0 = (float)y_first;
+  c.sR = (float)sR;
+  c.scale = (float)scale;
+  c.y0d = y_first;
+  c.sRd = sR;
+  c.origin = origin;
+  c.nb = nb;
+  c.out_sign = (float)((g->edge == DR_EDGE_LEADING ? 1.0 : -1.0) * (reverse ? -1.0 : 1.0));
+  return DR_OK;
+}

@@ -705,3 +705,94 @@ extern "C" dr_status dr_plan_check(const dr_plan_t *p) {
   }
   return DR_OK;
 }
+
+// ------------------------------------------- no-allocation entry point ---
+// The rows kernel with its geometry tables in a file-scope device array
+// instead of a plan's cudaMalloc'd block, for callers that may not allocate
+// device memory.  The array's host-side name is only a stand-in: the device
+// address comes from cudaGetSymbolAddress, once per device, on the first
+// call made with that device current.
+
+namespace dr {
+constexpr size_t kStaticScratchBytes = size_t(2) << 20;  // 2 MiB per device
+constexpr int kStaticMaxK = 16384;
+}  // namespace dr
+
+static __device__ __align__(256) unsigned char g_dr_static_scratch[dr::kStaticScratchBytes];
+
+namespace {
+std::mutex g_static_mu;                                    // guards the three below
+unsigned char g_static_stage[dr::kStaticScratchBytes];     // host staging (static)
+double g_static_tmp[2 * dr::kStaticMaxK];                  // host FP64 temporaries
+void *g_static_dev[64];                                    // device address per device
+}  // namespace
+
+extern "C" dr_status dr_reconstruct_rows_static(const dr_geometry *g, const double *wires,
+                                               int32_t K, const double *edges, int32_t B,
+                                               const uint16_t *d_images, float *d_out,
+                                               int32_t *d_status, dr_stream_t stream) {
+  if (K > kStaticMaxK) {
+    set_error("dr_reconstruct_rows_static: K = %d exceeds %d steps", K, kStaticMaxK);
+    return DR_ERR_BUDGET;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail("dr_reconstruct_rows_static: cudaGetDevice", e);
+  if (dev < 0 || dev >= 64) {
+    set_error("dr_reconstruct_rows_static: device %d out of range", dev);
+    return DR_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_dev[dev]) {
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_dr_static_scratch);
+    if (e != cudaSuccess || !ptr)
+      return cuda_fail("dr_reconstruct_rows_static: cudaGetSymbolAddress", e);
+    g_static_dev[dev] = ptr;
+  }
+  StaticTables st;
+  dr_status s = build_rows_tables(g, wires, K, edges, B, g_static_stage, kStaticScratchBytes,
+                                  g_static_tmp, &st);
+  if (s != DR_OK) return s;
+  if ((size_t)st.rows * st.cols == 0) return DR_OK;
+  if (!d_images || !d_out) {
+    set_error("dr_reconstruct_rows_static: null buffer");
+    return DR_ERR_INVALID_ARG;
+  }
+  if (((uintptr_t)d_out & (st.tune.ppt == 4 ? 15 : 3)) != 0 || ((uintptr_t)d_images & 1) != 0 ||
+      (st.tune.ppt == 4 && ((uintptr_t)d_images & 7) != 0)) {
+    set_error("dr_reconstruct_rows_static: misaligned buffer");
+    return DR_ERR_INVALID_ARG;
+  }
+  cudaStream_t cs = (cudaStream_t)stream;
+  unsigned char *base = static_cast<unsigned char *>(g_static_dev[dev]);
+  // the staged tables include a zeroed error word; pageable source: the call
+  // returns once the bytes are staged, so the host buffer may be reused
+  e = cudaMemcpyAsync(base, g_static_stage, st.bytes, cudaMemcpyHostToDevice, cs);
+  if (e != cudaSuccess) return cuda_fail("dr_reconstruct_rows_static: table upload", e);
+  if (d_status) {
+    e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), cs);
+    if (e != cudaSuccess) return cuda_fail("dr_reconstruct_rows_static: status clear", e);
+  }
+  dr_plan_t p{};
+  p.rows = st.rows;
+  p.cols = st.cols;
+  p.K = st.K;
+  p.B = st.B;
+  p.kernel = DR_KERNEL_ROWS;
+  p.out_dtype = DR_OUT_F32;
+  p.geom_prec = DR_GEOM_FP32;
+  p.c = st.c;
+  p.c.grp = reinterpret_cast<const GroupC *>(base + st.off_grp);
+  p.c.stp = reinterpret_cast<const StepC *>(base + st.off_stp);
+  p.c.efx = reinterpret_cast<const int32_t *>(base + st.off_efx);
+  p.c.err = d_status ? d_status : reinterpret_cast<int32_t *>(base + st.off_err);
+  p.tune = st.tune;
+  p.threads = st.threads;
+  p.smem_bytes = st.smem_bytes;
+  s = launch_reconstruct(&p, d_images, d_out, cs);
+  if (s != DR_OK) return s;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("dr_reconstruct_rows_static: launch", e);
+  return DR_OK;
+}

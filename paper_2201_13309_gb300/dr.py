@@ -29,7 +29,7 @@ KERNELS = {0: "rows", 1: "pixels"}
 EXPORTS = ("dr_plan", "dr_plan_destroy", "dr_plan_get_info", "dr_plan_device_bytes",
            "dr_reconstruct", "dr_reconstruct_host", "dr_image_differences",
            "dr_plan_depths", "dr_plan_check", "dr_status_string", "dr_last_error",
-           "dr_version")
+           "dr_version", "dr_reconstruct_rows_static")
 
 _d3 = ctypes.c_double * 3
 
@@ -95,6 +95,8 @@ def lib():
                 "dr_status_string": ([I32], ctypes.c_char_p),
                 "dr_last_error": ([], ctypes.c_char_p),
                 "dr_version": ([], ctypes.c_char_p),
+                "dr_reconstruct_rows_static": ([ctypes.POINTER(Geometry), P, I32, P, I32, P, P,
+                                                P, P], I32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -245,6 +247,24 @@ def image_differences(images, stream=None):
     check(lib().dr_image_differences(_dptr(images), K, H, W, _dptr(d),
                                      ctypes.c_void_p(_stream_handle(stream))))
     return d
+
+
+def reconstruct_rows_static(geom, wires, edges, images, out, status=None, edge="leading",
+                            stream=None):
+    """dr_reconstruct_rows_static: the rows kernel with no allocation at all.
+
+    images: CUDA [K, rows, cols] 16-bit; out: CUDA float32 [B, rows, cols]
+    (caller-allocated); status: optional CUDA int32 tensor of one element.
+    """
+    w = np.ascontiguousarray(wires, dtype=np.float64)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    g = geometry_struct(geom, edge)
+    check(lib().dr_reconstruct_rows_static(
+        ctypes.byref(g), w.ctypes.data_as(ctypes.c_void_p), w.shape[0],
+        e.ctypes.data_as(ctypes.c_void_p), e.shape[0] - 1,
+        None if images is None else _dptr(images), None if out is None else _dptr(out),
+        None if status is None else _dptr(status), ctypes.c_void_p(_stream_handle(stream))))
+    return out
 
 
 def version():
