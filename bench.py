@@ -46,7 +46,7 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "rows_kernel_full_detector_traf
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("dr_recon.cu", "dr_internal.h"):
+    for f in ("dr_device.cuh", "dr_tables.h"):
         with open(os.path.join(ROOT, "paper_2201_13309_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -232,6 +232,184 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_precision(args, spec, images, dev):
+    """Error of each arithmetic variant against the FP64 oracle on sampled
+    rows of the scan, the conservation error on every pixel whose depth range
+    lies inside the bins, and the exactness of the integer differences."""
+    import torch
+
+    from oracle import oracle as O
+    from paper_2201_13309_gb300 import dr
+
+    O.build()
+    H, W = spec.geom["rows"], spec.geom["cols"]
+    rows = [int(r) for r in np.linspace(0, H - 1, args.precision_rows)]
+    threads = os.cpu_count() or 1
+    host_rows, refs = {}, {}
+    for r in rows:
+        host_rows[r] = images[:, r:r + 1, :].cpu().numpy().view(np.uint16)
+        g = dict(spec.geom)
+        g["det_origin"] = (np.asarray(spec.geom["det_origin"])
+                           + r * np.asarray(spec.geom["row_step"])).tolist()
+        g["rows"] = 1
+        refs[r] = O.reconstruct(g, spec.wires, host_rows[r], spec.edges, threads=threads)
+    # integer differences, bit-exact check on the sampled rows
+    mism, checked = 0, 0
+    for r in rows:
+        d = dr.image_differences(images[:, r:r + 1, :].contiguous()).cpu().numpy()
+        mism += int(np.count_nonzero(d.astype(np.int64) != O.differences(host_rows[r])))
+        checked += d.size
+    # pixels whose whole depth range lies inside the bins (conservation holds)
+    g1 = dict(spec.geom, cols=1)
+    dd = O.depths(g1, spec.wires)[:, 0, [0, -1]]
+    inside = torch.from_numpy((dd[:, 0] > spec.edges[0]) & (dd[:, 1] < spec.edges[-1])).to(dev)
+    first = images[0].to(torch.int32) & 0xFFFF
+    last = images[-1].to(torch.int32) & 0xFFFF
+    sabs = torch.zeros((H, W), dtype=torch.float64, device=dev)
+    for k0 in range(0, spec.K - 1, 32):
+        k1 = min(spec.K - 1, k0 + 32)
+        a = images[k0:k1 + 1].to(torch.int32) & 0xFFFF
+        sabs += (a[:-1] - a[1:]).abs().sum(0).double()
+    variants = []
+    for geom_p in ("fp32", "fp64"):
+        for out_t in ("f32", "bf16"):
+            plan = dr.Plan(spec.geom, spec.wires, spec.edges, out_dtype=out_t,
+                           geom_precision=geom_p)
+            out = plan.empty_output(dev)
+            for _ in range(2):
+                plan.reconstruct(images, out)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.precision_reps):
+                plan.reconstruct(images, out)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / args.precision_reps
+            worst = 0.0
+            for r in rows:
+                got = out[:, r:r + 1, :].float().cpu().numpy().astype(np.float64)
+                s = np.abs(np.diff(host_rows[r].astype(np.int64), axis=0)).sum(0)[None]
+                worst = max(worst, float((np.abs(got - refs[r]) / np.maximum(s, 1)).max()))
+            tot = out.sum(0, dtype=torch.float64)
+            cons = ((tot - (first - last).double()).abs() / sabs.clamp(min=1))[inside, :]
+            variants.append({
+                "geometry": geom_p, "output": out_t, "ms": ms,
+                "GBps": plan.info()["bytes_per_call"] / ms / 1e6,
+                "max_bin_err_over_sum_abs_dI": worst,
+                "max_conservation_err_over_sum_abs_dI": float(cons.max()),
+                "meets_1e-4": worst <= 1e-4})
+            plan.close()
+            del out
+    return {"mode": "precision", "metric": "max |bin - oracle| / sum_k |dI_k| per pixel",
+            "workload": WORKLOAD, "oracle_rows": len(rows),
+            "conservation_pixels": int(inside.sum()) * W,
+            "differences": {"checked": checked, "mismatches": mism}, "variants": variants}
+
+
+def batch_waves(specs, budget_bytes):
+    """Greedy packing of scans (in order) into waves whose inputs + outputs
+    fit the HBM budget."""
+    waves, cur, used = [], [], 0
+    for sp in specs:
+        need = sp.P * (2 * sp.K + 4 * sp.B)
+        if cur and used + need > budget_bytes:
+            waves.append(cur)
+            cur, used = [], 0
+        cur.append(sp)
+        used += need
+    if cur:
+        waves.append(cur)
+    return waves
+
+
+def run_batched(args, dev):
+    """64 uneven scans: per-scan launch loop vs one persistent launch per wave
+    (replayed from a captured CUDA graph), same plans, same buffers."""
+    import torch
+
+    from paper_2201_13309_gb300 import autotune, dr, synth
+
+    specs = [synth.batch_scan_spec(s) for s in range(args.batch_scans)]
+    waves = batch_waves(specs, args.budget_gb * 1e9)
+    tot_loop = tot_batch = 0.0
+    units = bytes_alg = 0.0
+    per_wave = []
+    ok = True
+    for wave in waves:
+        jobs = []
+        for sp in wave:
+            img = synth.device_spot_images(sp.geom, sp.wires, sp.scat, seed=1000 + len(jobs),
+                                           background=20.0, device=dev)
+            out = torch.empty((sp.B, sp.geom["rows"], sp.geom["cols"]), device=dev)
+            plan, _ = autotune.tuned_plan(sp.geom, sp.wires, sp.edges, img, out=out, reps=3)
+            jobs.append((plan, img, out))
+            units += sp.P * sp.K
+            bytes_alg += plan.info()["bytes_per_call"]
+        batch, btune = autotune.tuned_batch(jobs)
+        # per-scan launch loop
+        for plan, img, out in jobs:
+            plan.reconstruct(img, out)
+        torch.cuda.synchronize()
+        ref = None
+        if args.check:  # sampled bin planes (bitwise) and the exact FP64 sum of each output
+            ref = []
+            for _, _, out in jobs:
+                sel = torch.linspace(0, out.shape[0] - 1, 8, device=dev).long()
+                ref.append((sel, out[sel].clone(), out.sum(dtype=torch.float64)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.batch_reps):
+            for plan, img, out in jobs:
+                plan.reconstruct(img, out)
+        e1.record()
+        e1.synchronize()
+        t_loop = e0.elapsed_time(e1) / args.batch_reps
+        for _, _, out in jobs:
+            out.fill_(float("nan"))
+        batch.launch()
+        torch.cuda.synchronize()
+        batch.check_device()
+        if ref is not None:
+            for (_, _, out), (sel, planes, total) in zip(jobs, ref):
+                ok &= bool(torch.equal(out[sel].view(torch.int32), planes.view(torch.int32)))
+                ok &= bool(torch.equal(out.sum(dtype=torch.float64), total))
+            del ref
+        e0.record()
+        for _ in range(args.batch_reps):
+            batch.launch()
+        e1.record()
+        e1.synchronize()
+        t_batch = e0.elapsed_time(e1) / args.batch_reps
+        tot_loop += t_loop
+        tot_batch += t_batch
+        per_wave.append({"scans": len(wave), "loop_ms": t_loop, "batch_ms": t_batch,
+                         "items": batch.info()["items"], "ctas_per_sm": btune["ctas_per_sm"],
+                         "max_tile_cols": btune["max_tile_cols"]})
+        batch.close()
+        for plan, img, out in jobs:
+            plan.close()
+        del jobs, img, out
+        torch.cuda.empty_cache()
+    n = len(specs)
+    peak, kind = measured_hbm_peak()
+    return {
+        "mode": "batched", "metric": "scans/s", "scans": n, "waves": len(waves),
+        "budget_GB": args.budget_gb,
+        "loop": {"scans_per_s": n / (tot_loop * 1e-3), "ms": tot_loop,
+                 "pixel_steps_per_s": units / (tot_loop * 1e-3),
+                 "GBps": bytes_alg / (tot_loop * 1e-3) / 1e9},
+        "batch": {"scans_per_s": n / (tot_batch * 1e-3), "ms": tot_batch,
+                  "pixel_steps_per_s": units / (tot_batch * 1e-3),
+                  "GBps": bytes_alg / (tot_batch * 1e-3) / 1e9,
+                  "hbm_frac": bytes_alg / (tot_batch * 1e-3) / 1e9 / peak},
+        "speedup": tot_loop / tot_batch, "bitwise_equal": ok if args.check else None,
+        "peak_GBps": peak, "peak_kind": kind, "per_wave": per_wave,
+        "workload": ("64 uneven scans (seeds 0-63): ROI in {256^2, 512^2, 1024^2, 2048x1024, "
+                     "2048^2}, 51-801 steps, bins of 0.5/1/2 um over +-400 um, FP32"),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -242,6 +420,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--mode", default="plain", choices=["plain", "precision", "batched"])
+    ap.add_argument("--batch-scans", type=int, default=64)
+    ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--check", action="store_true", help="batched: compare outputs bitwise")
+    ap.add_argument("--precision-rows", type=int, default=24)
+    ap.add_argument("--precision-reps", type=int, default=20)
     ap.add_argument("--tile-cols", type=int, default=0, help="fixed tile width (0: autotune)")
     ap.add_argument("--bin-groups", type=int, default=0)
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
@@ -272,6 +457,11 @@ def main():
         tdist.barrier()
         __graft_entry__.build()
 
+    if args.mode == "batched":
+        if rank == 0:
+            print(json.dumps(run_batched(args, dev)), flush=True)
+        return 0
+
     spec = synth.full_scan_spec(0)
     if args.rows != spec.geom["rows"]:
         spec.geom = dict(spec.geom, rows=args.rows)
@@ -280,6 +470,11 @@ def main():
                                      spec.scat.spot_row[keep], spec.scat.spot_col[keep])
     images = synth.device_spot_images(spec.geom, spec.wires, spec.scat, seed=rank, background=20.0,
                                       device=dev)
+    if args.mode == "precision":
+        if rank == 0:
+            print(json.dumps(run_precision(args, spec, images, dev)), flush=True)
+        return 0
+
     from paper_2201_13309_gb300 import autotune
 
     out = torch.empty((spec.B, spec.geom["rows"], spec.geom["cols"]), dtype=torch.float32,

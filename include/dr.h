@@ -162,6 +162,55 @@ dr_status dr_plan_depths(const dr_plan_t *plan, int32_t r0, int32_t nrows,
  * wait ran out).  Synchronizes the device.  DR_OK or DR_ERR_TIMEOUT. */
 dr_status dr_plan_check(const dr_plan_t *plan);
 
+/* ---- Many scans in one persistent launch ---------------------------------
+ * A batch reconstructs several scans (each with its own plan, image stack and
+ * output; different ROI sizes, step and bin counts) in ONE launch of a
+ * persistent kernel: every CTA takes (scan, row, tile) work items from a device
+ * counter until none are left, biggest items first, so uneven scans do not
+ * leave the GPU idle between per-scan launches.  The counter reset and the
+ * launch are captured into a CUDA graph at creation; dr_batch_launch replays
+ * it.  Jobs must use rows-kernel plans (columns along the wire axis) with FP32
+ * geometry, widths that are multiples of 8, 16-byte aligned buffers and one
+ * output type.  The buffers are bound at creation: a batch always reads and
+ * writes the same device buffers (refill the image buffers between launches).
+ * The result of every scan is bitwise identical to dr_reconstruct's. */
+typedef struct {
+  const dr_plan_t *plan;
+  const uint16_t *d_images;   /* [K][rows][cols] of the plan, device */
+  void *d_out;                /* [B][rows][cols] of the plan, device */
+} dr_job;
+
+typedef struct dr_batch dr_batch_t;
+
+/* Optional batch settings; null means all zero (defaults). */
+typedef struct {
+  int32_t ctas_per_sm;        /* 1 (default, up to 227 KB of shared memory per
+                                 CTA) or 2 (up to 113 KB each: narrower tiles,
+                                 two CTAs overlapping on each SM) */
+  int32_t max_tile_cols;      /* cap on each job's tile width; 0 = the plan's */
+  int32_t reserved[2];
+} dr_batch_options;
+
+typedef struct {
+  int32_t scans;
+  int64_t items;              /* (scan, row, tile) work items */
+  int32_t grid, threads, smem_bytes;
+  size_t device_bytes;
+} dr_batch_info;
+
+/* Build descriptors, upload them and capture the launch graph (allocates a
+ * few KB of device memory; synchronous).  Each job keeps its plan's tile
+ * width, narrowed until it fits the per-CTA shared-memory budget of
+ * options->ctas_per_sm.  The plans must outlive the batch. */
+dr_status dr_batch_create(const dr_job *jobs, int32_t n, const dr_batch_options *options,
+                          dr_batch_t **out);
+/* Replay the captured launch on stream (asynchronous). */
+dr_status dr_batch_launch(dr_batch_t *batch, dr_stream_t stream);
+/* Synchronize, read and clear the batch's device error word. */
+dr_status dr_batch_check(dr_batch_t *batch);
+dr_status dr_batch_get_info(const dr_batch_t *batch, dr_batch_info *info);
+void dr_batch_destroy(dr_batch_t *batch);
+
 /* ---- Reconstruction that allocates nothing -------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that
  * cannot call cudaMalloc themselves and so cannot build a plan (dr_plan keeps

@@ -108,9 +108,58 @@ def tune(geom, wires, edges, images, out=None, edge="leading", out_dtype="f32",
 
 
 def tuned_plan(geom, wires, edges, images, **kw):
-    """A Plan with the autotuned launch shape."""
+    """A Plan with the autotuned launch shape.  A cached shape tuned on a
+    scan of the same class may not fit this one's shared memory (more steps
+    in the same bucket); the scan is then tuned on its own."""
     plan_kw = {k: kw[k] for k in ("edge", "out_dtype", "geom_precision", "force_pixels")
                if k in kw}
     best = tune(geom, wires, edges, images, **kw)
-    return dr.Plan(geom, wires, edges, tile_cols=best["tile_cols"],
-                   bin_groups=best["bin_groups"], **plan_kw), best
+    try:
+        plan = dr.Plan(geom, wires, edges, tile_cols=best["tile_cols"],
+                       bin_groups=best["bin_groups"], **plan_kw)
+    except dr.DrError:
+        if not best.get("cached"):
+            raise
+        kw = dict(kw, use_cache=False)
+        best = tune(geom, wires, edges, images, **kw)
+        plan = dr.Plan(geom, wires, edges, tile_cols=best["tile_cols"],
+                       bin_groups=best["bin_groups"], **plan_kw)
+    return plan, best
+
+
+BATCH_CANDIDATES = ((1, 0), (2, 0), (2, 64))   # (CTAs per SM, tile cap)
+
+
+def tuned_batch(jobs, reps=2, stream=None):
+    """The fastest batch build of these (plan, images, out) jobs: each
+    candidate (CTAs per SM, tile-width cap) is built, replayed `reps` times
+    and timed with CUDA events; the others are destroyed.  Returns
+    (batch, timings)."""
+    import torch
+
+    stream = stream or torch.cuda.current_stream()
+    best, timings = None, []
+    for per_sm, cap in BATCH_CANDIDATES:
+        try:
+            b = dr.Batch(jobs, ctas_per_sm=per_sm, max_tile_cols=cap)
+        except dr.DrError:
+            continue
+        b.launch(stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            b.launch(stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        timings.append({"ctas_per_sm": per_sm, "max_tile_cols": cap, "ms": ms})
+        if best is None or ms < best[0]:
+            if best is not None:
+                best[1].close()
+            best = (ms, b, per_sm, cap)
+        else:
+            b.close()
+    if best is None:
+        raise RuntimeError("no batch configuration accepted")
+    return best[1], {"ctas_per_sm": best[2], "max_tile_cols": best[3], "candidates": timings}

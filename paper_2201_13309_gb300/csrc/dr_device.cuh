@@ -1,0 +1,529 @@
+// Device code of the reconstruction: PTX helpers, the depth model, the two
+// reconstruction kernels and two small helper kernels (sm_103a).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "dr_tables.h"
+#include "../../include/dr.h"
+
+namespace dr {
+
+// ------------------------------------------------------------------ PTX ---
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Wait for the TMA phase with a time limit.  On timeout the error word is
+// set, the copies in flight get a second bounded wait to land, and the caller
+// returns without touching the tile.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+__device__ inline bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int32_t *err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > kWaitLimitNs) {
+      atomicExch(err, kDevTmaTimeout);
+      uint64_t t1 = global_ns();
+      while (!mbar_try_wait(bar, parity) && global_ns() - t1 < kWaitLimitNs) {
+      }
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void st_cs(float *p, float v) {
+  asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cs4(float *p, float a, float b, float c, float d) {
+  asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+__device__ __forceinline__ void st_cs(__nv_bfloat16 *p, float v) {
+  __nv_bfloat16 h = __float2bfloat16_rn(v);
+  unsigned short u = *reinterpret_cast<unsigned short *>(&h);
+  asm volatile("st.global.cs.b16 [%0], %1;" ::"l"(p), "h"(u) : "memory");
+}
+__device__ __forceinline__ void st_cs4(__nv_bfloat16 *p, float a, float b, float c, float d) {
+  __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  uint32_t ul = *reinterpret_cast<uint32_t *>(&lo), uh = *reinterpret_cast<uint32_t *>(&hi);
+  asm volatile("st.global.cs.v2.b32 [%0], {%1, %2};" ::"l"(p), "r"(ul), "r"(uh) : "memory");
+}
+
+// --------------------------------------------------------- depth model ---
+
+// FP32 depth position of (group, step) in fixed point (see dr_internal.h).
+__device__ __forceinline__ int32_t depth_fx(const GroupC &g, const StepC &s, const Consts &c) {
+  const float z = s.zf;
+  float inv = g.invD;
+  float a = __fmul_rn(c.y0, z);
+  if (c.has_eta) {
+    inv = rcp_approx(__fsub_rn(g.D, s.eta));
+    a = __fmaf_rn(s.eta, __fadd_rn(__fsub_rn(z, g.Z), g.Q0f), a);
+  }
+  const float tap = __fmaf_rn(a, inv, __fadd_rn(z, g.Q0f));
+  const float u = __fsub_rn(g.Z, tap);
+  const float L = sqrt_approx(__fmaf_rn(u, u, g.Y2));
+  const float num = __fmul_rn(tap, __fsub_rn(tap, __fadd_rn(g.Z, g.Z)));
+  const float dL = __fmul_rn(num, rcp_approx(__fadd_rn(L, g.L0)));
+  const float rem = __fmul_rn(__fmaf_rn(c.sR, dL, a), inv);
+  const int32_t rfx = __float2int_rn(__fmul_rn(rem, c.scale));
+  return (int32_t)((uint32_t)s.zfx + (uint32_t)g.Q0fx + (uint32_t)rfx);
+}
+
+// FP64 depth position of (group, step) relative to the plan origin.
+__device__ __forceinline__ double depth_f64(const GroupD &g, const StepD &s, const Consts &c) {
+  const double z = s.z, Dm = g.D - s.eta;
+  const double a = c.y0d * z + s.eta * (z - g.Z + g.Q0);
+  double rem = a / Dm;
+  for (int it = 0; it < 2; ++it) {
+    const double t = z + g.Q0 + rem;
+    const double u = g.Z - t;
+    const double L = sqrt(g.Y2 + u * u);
+    const double dL = t * (t - 2.0 * g.Z) / (L + g.L0);
+    rem = (a + c.sRd * dL) / Dm;
+  }
+  return ((z - c.origin) + g.Q0) + rem;
+}
+
+struct GeoFx {
+  using pos_t = int32_t;
+  using step_t = StepC;
+  using group_t = GroupC;
+  static __device__ __forceinline__ const StepC *steps(const Consts &c) { return c.stp; }
+  static __device__ __forceinline__ const GroupC &group(const Consts &c, int i) {
+    return c.grp[i];
+  }
+  static __device__ __forceinline__ pos_t depth(const GroupC &g, const StepC &s,
+                                                const Consts &c) {
+    return depth_fx(g, s, c);
+  }
+  static __device__ __forceinline__ pos_t edge(const Consts &c, int j) { return c.efx[j]; }
+  // 1 / (b - a) for a < b (approximate reciprocal; same value in both kernels)
+  static __device__ __forceinline__ float inv_len(pos_t a, pos_t b) {
+    return rcp_approx(__int2float_rn(b - a));
+  }
+  static __device__ __forceinline__ float frac(pos_t e, pos_t a, float inv) {
+    float f = __fmul_rn(__int2float_rn(e - a), inv);
+    return fminf(fmaxf(f, 0.f), 1.f);
+  }
+  static __device__ __forceinline__ double to_mm(pos_t p, const Consts &c) {
+    return ((double)p / (double)c.scale + c.origin) / c.nb;
+  }
+};
+
+struct GeoF64 {
+  using pos_t = double;
+  using step_t = StepD;
+  using group_t = GroupD;
+  static __device__ __forceinline__ const StepD *steps(const Consts &c) { return c.stp64; }
+  static __device__ __forceinline__ const GroupD &group(const Consts &c, int i) {
+    return c.grp64[i];
+  }
+  static __device__ __forceinline__ pos_t depth(const GroupD &g, const StepD &s,
+                                                const Consts &c) {
+    return depth_f64(g, s, c);
+  }
+  static __device__ __forceinline__ pos_t edge(const Consts &c, int j) { return c.e64[j]; }
+  static __device__ __forceinline__ double inv_len(pos_t a, pos_t b) { return 1.0 / (b - a); }
+  static __device__ __forceinline__ float frac(pos_t e, pos_t a, double inv) {
+    double f = (e - a) * inv;
+    return (float)fmin(fmax(f, 0.0), 1.0);
+  }
+  static __device__ __forceinline__ double to_mm(pos_t p, const Consts &c) {
+    return (p + c.origin) / c.nb;
+  }
+};
+
+// ------------------------------------------------------ pixel values ---
+// A uint16 count x is held as the float 2^23 + x (bit pattern 0x4B00_0000 | x):
+// exact, and differences of two such values are the exact integer
+// differences (|x - y| < 2^16 << 2^24).
+__device__ __forceinline__ float biased_lo(uint32_t w) {
+  return __uint_as_float(__byte_perm(w, 0x4B00u, 0x5410));
+}
+__device__ __forceinline__ float biased_hi(uint32_t w) {
+  return __uint_as_float(__byte_perm(w, 0x4B00u, 0x5432));
+}
+__device__ __forceinline__ float biased(uint16_t x) {
+  return __uint_as_float(0x4B000000u | (uint32_t)x);
+}
+
+// Exact difference I_k - I_{k+1} as the kernels form it.
+__device__ __forceinline__ float step_delta(uint16_t a, uint16_t b) {
+  return __fsub_rn(biased(a), biased(b));
+}
+
+template <int PPT>
+__device__ __forceinline__ void load_px(const uint16_t *p, float (&v)[PPT]) {
+  if constexpr (PPT == 4) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    v[0] = biased_lo(u.x);
+    v[1] = biased_hi(u.x);
+    v[2] = biased_lo(u.y);
+    v[3] = biased_hi(u.y);
+  } else {
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) v[i] = biased(p[i]);
+  }
+}
+
+template <class OutT, int PPT>
+__device__ __forceinline__ void store_px(OutT *p, const float (&v)[PPT]) {
+  if constexpr (PPT == 4) {
+    st_cs4(p, v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) st_cs(p + i, v[i]);
+  }
+}
+
+__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Stage the image tile [K][1][tile_cols] (row `row`, columns c0..) into
+// smem: by TMA (thread 0 arms the already initialised mbarrier `bar` and
+// issues the chunk copies) or with plain loads (zero-filled tail).
+template <bool kTma>
+__device__ __forceinline__ void stage_tile(const CUtensorMap *tmap, const uint16_t *img,
+                                           uint16_t *simg, uint64_t *bar, const Consts &c,
+                                           const Tuning &t, int row, int c0) {
+  const int TC = t.tile_cols;
+  if constexpr (kTma) {
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, (uint32_t)(t.kc * t.nchunks * TC * 2));
+      for (int ch = 0; ch < t.nchunks; ++ch)
+        tma_load_3d(simg + (size_t)ch * t.kc * TC, tmap, bar, c0, row, ch * t.kc);
+    }
+  } else {
+    const int n = c.K * TC;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int k = i / TC, cc = i - k * TC, col = c0 + cc;
+      simg[i] = col < c.W ? img[((size_t)k * c.H + row) * c.W + col] : (uint16_t)0;
+    }
+  }
+}
+
+// --------------------------------------------------------- rows kernel ---
+// Shared-memory layout of one rows tile: [0, 128) mbarrier, two counters and
+// the persistent kernel's work slot; then the image tile [Kpad][tile_cols]
+// uint16, the row's depth positions [K], and the (k, f) table [B + 1].
+
+// One tile: row `row`, columns c0 .. c0 + tile_cols - 1, all steps and bins.
+// The mbarrier at smem[0] must be initialised; `parity` is its phase for this
+// tile.  Returns false (for every thread of the CTA) if the bounded TMA wait
+// ran out; the tile is then left unwritten and the error word is set.
+template <class Geo, class OutT, bool kTma, int PPT>
+__device__ __forceinline__ bool rows_tile(const CUtensorMap *tmap, const uint16_t *img,
+                                          OutT *out, const Consts &c, const Tuning &t,
+                                          int row, int c0, unsigned char *smem,
+                                          uint32_t parity) {
+  using pos_t = typename Geo::pos_t;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  int *zcount = reinterpret_cast<int *>(smem + 8);
+  uint16_t *simg = reinterpret_cast<uint16_t *>(smem + 128);
+  const int TC = t.tile_cols, K = c.K, B = c.B;
+  const int Kpad = t.kc * t.nchunks;
+  pos_t *spos = reinterpret_cast<pos_t *>(smem + 128 + align16((size_t)Kpad * TC * 2));
+  int2 *stab = reinterpret_cast<int2 *>(reinterpret_cast<unsigned char *>(spos) +
+                                        align16((size_t)K * sizeof(pos_t)));
+  const int tid = threadIdx.x, NT = blockDim.x;
+
+  stage_tile<kTma>(tmap, img, simg, bar, c, t, row, c0);
+  if (tid == 0) zcount[0] = zcount[1] = 0;
+  // depth positions of this row (processing order: increasing depth)
+  const auto &g = Geo::group(c, row);
+  const auto *steps = Geo::steps(c);
+  for (int k = tid; k < K; k += NT) spos[k] = Geo::depth(g, steps[k], c);
+  __syncthreads();
+  // each bin edge -> (k, f): k = last step below the edge (clamped to an
+  // interval), f = position of the edge inside [d_k, d_{k+1}], clamped.
+  // Edges at or below d_0 give F = 0 and edges at or above d_{K-1} give
+  // F = S_{K-1}, so only bins [nz_lo, nz_hi) can hold data.
+  int below = 0, above = 0;
+  const pos_t tfirst = spos[0], tlast = spos[K - 1];
+  for (int j = tid; j <= B; j += NT) {
+    const pos_t e = Geo::edge(c, j);
+    int lo = 0, hi = K;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (spos[mid] < e) lo = mid + 1; else hi = mid;
+    }
+    const int k = min(max(lo - 1, 0), K - 2);
+    const float f = Geo::frac(e, spos[k], Geo::inv_len(spos[k], spos[k + 1]));
+    stab[j] = make_int2(k, __float_as_int(f));
+    below += !(e > tfirst);
+    above += !(e < tlast);
+  }
+  if (below) atomicAdd(&zcount[0], below);
+  if (above) atomicAdd(&zcount[1], above);
+  __syncthreads();
+  const int nz_hi = min(B + 1 - zcount[1], B);
+  const int nz_lo = min(max(zcount[0] - 1, 0), nz_hi);
+  if constexpr (kTma) {
+    const bool late = !mbar_wait_bounded(bar, parity, c.err);
+    if (__syncthreads_or(late)) return false;
+  }
+
+  // stream the bins; thread = PPT adjacent pixels; the zero ranges and the
+  // data range are each split evenly over the bin groups
+  const int lanes = TC / PPT;
+  const int lane = tid % lanes, grp = tid / lanes;
+  const int lc = lane * PPT, col = c0 + lc;
+  if (col >= c.W || grp >= t.bin_groups) return true;
+  const int G = t.bin_groups;
+  auto slice_lo = [&](int lo, int hi) { return lo + (int)((long long)(hi - lo) * grp / G); };
+  auto slice_hi = [&](int lo, int hi) { return lo + (int)((long long)(hi - lo) * (grp + 1) / G); };
+  const float sign = c.out_sign;
+  const size_t plane = (size_t)c.H * c.W;
+  OutT *const o0 = out + (size_t)row * c.W + col;
+  float zero[PPT];
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) zero[i] = __fmul_rn(sign, 0.f);
+  auto zero_fill = [&](int a, int b) {
+    OutT *o = o0 + (size_t)a * plane;
+#pragma unroll 4
+    for (int j = a; j < b; ++j, o += plane) store_px<OutT, PPT>(o, zero);
+  };
+  zero_fill(slice_lo(0, nz_lo), slice_hi(0, nz_lo));
+  zero_fill(slice_lo(nz_hi, B), slice_hi(nz_hi, B));
+
+  const int a = slice_lo(nz_lo, nz_hi), b = slice_hi(nz_lo, nz_hi);
+  if (a >= b) return true;
+  const bool rev = c.reverse != 0;
+  auto srow = [&](int k) { return simg + (size_t)(rev ? K - 1 - k : k) * TC + lc; };
+  float I0[PPT];
+  load_px<PPT>(srow(0), I0);
+  auto evalF = [&](int2 kf, float (&F)[PPT]) {
+    float x[PPT], y[PPT];
+    load_px<PPT>(srow(kf.x), x);
+    load_px<PPT>(srow(kf.x + 1), y);
+    const float f = __int_as_float(kf.y);
+#pragma unroll
+    for (int i = 0; i < PPT; ++i)
+      F[i] = __fmaf_rn(f, __fsub_rn(x[i], y[i]), __fsub_rn(I0[i], x[i]));
+  };
+  float Fp[PPT];
+  evalF(stab[a], Fp);
+  OutT *o = o0 + (size_t)a * plane;
+#pragma unroll 4
+  for (int j = a; j < b; ++j, o += plane) {
+    float Fn[PPT], v[PPT];
+    evalF(stab[j + 1], Fn);
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      v[i] = __fmul_rn(sign, __fsub_rn(Fn[i], Fp[i]));
+      Fp[i] = Fn[i];
+    }
+    store_px<OutT, PPT>(o, v);
+  }
+  return true;
+}
+
+// One CTA per tile (grid: tiles along the row x rows).
+template <class Geo, class OutT, bool kTma, int PPT>
+__global__ void __launch_bounds__(512) rows_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                   const uint16_t *__restrict__ img,
+                                                   OutT *__restrict__ out, const Consts c,
+                                                   const Tuning t) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if constexpr (kTma) {
+    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
+  }
+  rows_tile<Geo, OutT, kTma, PPT>(&tmap, img, out, c, t, blockIdx.y, blockIdx.x * t.tile_cols,
+                                  smem, 0u);
+}
+
+// ------------------------------------------------- persistent batch kernel ---
+// Many scans (each with its own plan tables, tensor map and tile shape) in
+// one launch: every CTA takes (scan, row, tile) work items from a device
+// counter until none are left.  Items are numbered scan by scan in the order
+// of the descriptor array.
+
+struct BatchScan {
+  CUtensorMap tmap;        // [K][rows][cols] images, box [kc][1][tile_cols]
+  const uint16_t *img;
+  void *out;
+  Consts c;
+  Tuning t;
+  long long item_begin;    // first work item of this scan
+  int tiles_per_row;
+  int pad;
+};
+
+template <class OutT>
+__global__ void __launch_bounds__(512, 1) batch_rows_kernel(const BatchScan *__restrict__ scans,
+                                                            int nscans, long long n_items,
+                                                            unsigned long long *counter) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  long long *slot = reinterpret_cast<long long *>(smem + 16);
+  int *sscan = reinterpret_cast<int *>(smem + 24);
+  if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
+  uint32_t parity = 0;
+  for (;;) {
+    __syncthreads();  // previous tile done with smem; barrier initialised
+    if (threadIdx.x == 0) {
+      const long long item = (long long)atomicAdd(counter, 1ull);
+      int lo = 0, hi = nscans - 1;  // last scan with item_begin <= item
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (scans[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+      }
+      *slot = item;
+      *sscan = lo;
+    }
+    __syncthreads();
+    const long long item = *slot;
+    if (item >= n_items) break;
+    const BatchScan &S = scans[*sscan];
+    const long long local = item - S.item_begin;
+    const int row = (int)(local / S.tiles_per_row);
+    const int c0 = (int)(local % S.tiles_per_row) * S.t.tile_cols;
+    if (!rows_tile<GeoFx, OutT, true, 4>(&S.tmap, S.img, reinterpret_cast<OutT *>(S.out), S.c,
+                                         S.t, row, c0, smem, parity))
+      break;
+    parity ^= 1u;
+  }
+}
+
+// ------------------------------------------------------- pixels kernel ---
+
+template <class Geo, class OutT, bool kTma>
+__global__ void __launch_bounds__(256) pixels_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                     const uint16_t *__restrict__ img,
+                                                     OutT *__restrict__ out, const Consts c,
+                                                     const Tuning t) {
+  using pos_t = typename Geo::pos_t;
+  using step_t = typename Geo::step_t;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  uint16_t *simg = reinterpret_cast<uint16_t *>(smem + 128);
+  const int TC = t.tile_cols, K = c.K, B = c.B;
+  const int Kpad = t.kc * t.nchunks;
+  step_t *sstep = reinterpret_cast<step_t *>(smem + 128 + align16((size_t)Kpad * TC * 2));
+  pos_t *sedge = reinterpret_cast<pos_t *>(reinterpret_cast<unsigned char *>(sstep) +
+                                           align16((size_t)K * sizeof(step_t)));
+  const int row = blockIdx.y, c0 = blockIdx.x * TC;
+  const int tid = threadIdx.x, NT = blockDim.x;
+
+  if constexpr (kTma) {
+    if (tid == 0) mbar_init(bar, 1);
+  }
+  stage_tile<kTma>(&tmap, img, simg, bar, c, t, row, c0);
+  const step_t *gsteps = Geo::steps(c);
+  for (int k = tid; k < K; k += NT) sstep[k] = gsteps[k];
+  for (int j = tid; j <= B; j += NT) sedge[j] = Geo::edge(c, j);
+  __syncthreads();
+  if constexpr (kTma) {
+    if (!mbar_wait_bounded(bar, 0, c.err)) return;
+  }
+  const int col = c0 + tid;
+  if (col >= c.W) return;
+  const auto g = Geo::group(c, row * c.W + col);
+  const bool rev = c.reverse != 0;
+  auto spx = [&](int k) { return biased(simg[(size_t)(rev ? K - 1 - k : k) * TC + tid]); };
+
+  // lockstep merge-walk: every lane handles bin edge j together, each with
+  // its own step pointer k (t0 = d_k, t1 = d_{k+1})
+  int k = 0;
+  pos_t t0 = Geo::depth(g, sstep[0], c), t1 = Geo::depth(g, sstep[1], c);
+  auto inv = Geo::inv_len(t0, t1);
+  const float I0 = spx(0);
+  float Ik = I0, Ik1 = spx(1);
+  const float sign = c.out_sign;
+  const size_t plane = (size_t)c.H * c.W;
+  OutT *o = out + (size_t)row * c.W + col;
+  float Fp = 0.f;
+  for (int j = 0; j <= B; ++j) {
+    const pos_t e = sedge[j];
+    while (k < K - 2 && t1 < e) {
+      ++k;
+      t0 = t1;
+      t1 = Geo::depth(g, sstep[k + 1], c);
+      inv = Geo::inv_len(t0, t1);
+      Ik = Ik1;
+      Ik1 = spx(k + 1);
+    }
+    const float f = Geo::frac(e, t0, inv);
+    const float F = __fmaf_rn(f, __fsub_rn(Ik, Ik1), __fsub_rn(I0, Ik));
+    if (j > 0) {
+      st_cs(o, __fmul_rn(sign, __fsub_rn(F, Fp)));
+      o += plane;
+    }
+    Fp = F;
+  }
+}
+
+// ------------------------------------------------ small helper kernels ---
+
+template <class Geo>
+__global__ void depths_kernel(const Consts c, int kernel, int r0, int nrows, double *out) {
+  const long long n = (long long)nrows * c.W * c.K;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i % c.K);
+    const long long pc = i / c.K;
+    const int col = (int)(pc % c.W), r = r0 + (int)(pc / c.W);
+    const int gi = kernel == DR_KERNEL_ROWS ? r : r * c.W + col;
+    const int kp = c.reverse ? c.K - 1 - k : k;
+    out[i] = Geo::to_mm(Geo::depth(Geo::group(c, gi), Geo::steps(c)[kp], c), c);
+  }
+}
+
+}  // namespace dr

@@ -1,91 +1,13 @@
-// Internal definitions shared by the library's translation units.
-//
-// Depth model (the tangent geometry of the differential-aperture method; the
-// paper's Sec. III-C "pixel reconstruction function" assigns each difference
-// to depth): everything is projected onto the plane perpendicular to the wire
-// axis, with e2 along the projected beam and e1 toward the first wire centre.
-// A beam point at projected depth t sits at (0, t); pixel p at (Y, Z); wire
-// step k at (y_k, z_k), radius R.  The line from (0, t) to (Y, Z) touches the
-// wire circle on the chosen edge (sign s = +-1) when
-//
-//     t (Y - y_k) = z_k Y - Z y_k + s R L(t),   L(t) = sqrt(Y^2 + (Z - t)^2).
-//
-// With y0 = y_0, eta_k = y_k - y0, D = Y - y0, L0 = sqrt(Y^2 + Z^2),
-// dL(t) = L(t) - L0 = t (t - 2Z) / (L(t) + L0) and
-// Q0 = (-y0 Z + s R L0) / D this is exactly
-//
-//     t_k = z_k + Q0 + (a_k + s R dL(t_k)) / (D - eta_k),
-//     a_k = y0 z_k + eta_k (z_k - Z + Q0).
-//
-// z_k and Q0 are large (up to ~1 mm) and come from FP64; the remainder term
-// is small (~5e-4 mm in the beamline set-up) and is all that FP32 computes
-// per (pixel, step).  Positions are held as 32-bit fixed point in units of
-// 2^-shift mm of projected depth relative to a plan origin, so differences of
-// positions are exact.  dL enters scaled by R / D ~ 5e-5, so evaluating it
-// at the estimate without the dL term leaves an error ~1e-10 mm.
+// Host-side internals shared by the library's translation units.
 #pragma once
 
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
+
 #include "../../include/dr.h"
-
-namespace dr {
-
-// Per geometry group (a detector row when all pixels of a row share their
-// projected position, else a single pixel).
-struct GroupC {
-  float Z, Y2, L0, invD;   // FP32 copies of FP64 values
-  float D, Q0f;
-  int32_t Q0fx;            // round(Q0 * 2^shift)
-  float pad;
-};
-static_assert(sizeof(GroupC) == 32, "GroupC layout");
-
-struct StepC {
-  float zf, eta;           // z_k, eta_k (FP32)
-  int32_t zfx;             // round((z_k - origin) * 2^shift)
-  float pad;
-};
-static_assert(sizeof(StepC) == 16, "StepC layout");
-
-// FP64 mirrors for the all-FP64 geometry variant.
-struct GroupD {
-  double Z, Y2, L0, D, Q0;
-};
-struct StepD {
-  double z, eta;           // z_k - origin is formed on the fly
-};
-
-// Everything a reconstruction kernel needs besides the images/output.
-struct Consts {
-  const GroupC *grp;
-  const StepC *stp;
-  const int32_t *efx;      // [B+1] fixed-point edges (projected depth)
-  const GroupD *grp64;
-  const StepD *stp64;
-  const double *e64;       // [B+1] edges relative to origin (projected depth)
-  int K, H, W, B;
-  int has_eta;             // wire centres do not all share y
-  int reverse;             // plan's step order is the reverse of the images'
-  float y0, sR, scale;     // y0, s*R, 2^shift
-  double y0d, sRd, origin;  // origin of the fixed-point positions (mm)
-  double nb;               // |projected unit beam direction|: d = t / nb
-  float out_sign;          // +1 leading/forward; -1 trailing or reversed
-  int32_t *err;            // device error word
-};
-
-// Error codes written to the device error word.
-enum : int32_t { kDevOk = 0, kDevTmaTimeout = 1 };
-
-struct Tuning {
-  int tile_cols;           // pixels per CTA along the row
-  int ppt;                 // pixels per thread (1 or 4)
-  int bin_groups;          // thread groups splitting the bins
-  int kc, nchunks;         // TMA step chunk and chunk count
-};
-
-}  // namespace dr
+#include "dr_tables.h"
 
 struct dr_plan {
   int rows, cols, K, B, edge;
@@ -119,6 +41,22 @@ struct StaticTables {
 dr_status build_rows_tables(const dr_geometry *g, const double *wires, int K,
                             const double *edges, int B, unsigned char *stage, size_t cap,
                             double *tmp, StaticTables *out);
+
+constexpr int kSmemPerSm = 228 * 1024;       // shared memory per SM
+constexpr int kSmemPerCtaMax = 227 * 1024;   // opt-in maximum per CTA
+
+// Shared-memory bytes of one rows / pixels tile (layouts in dr_device.cuh).
+int rows_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64);
+int pixels_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64);
+// TMA chunking of K steps for a tile width (128-byte aligned destinations).
+void choose_chunks(int K, int tile_cols, int *kc, int *nchunks);
+// Raise a kernel's dynamic shared-memory limit (once per device).
+dr_status allow_smem(const void *fn);
+// [K][rows][cols] uint16 tensor map with a [kc][1][tile_cols] box (p->tune).
+dr_status make_tensor_map(const dr_plan_t *p, const uint16_t *img, CUtensorMap *tm);
+// Reconstruction launch of a plan (defined with the kernels).
+dr_status launch_reconstruct(const dr_plan_t *p, const uint16_t *img, void *out,
+                             struct CUstream_st *st);
 
 void set_error(const char *fmt, ...);
 dr_status cuda_fail(const char *what, int err);

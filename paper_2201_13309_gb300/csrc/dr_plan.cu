@@ -72,12 +72,13 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 using namespace dr;
 
 namespace {
-
 struct Group64 {
   double Y, Z, D, L0, Q0;
 };
+}  // namespace
 
-// Launch shape: smem layout sizes for the two kernels (see dr_recon.cu).
+namespace dr {
+// Launch shape: smem layout sizes for the two kernels (see dr_device.cuh).
 int rows_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64) {
   size_t s = 128;                                          // mbarrier slot
   s += align_up((size_t)Kpad * tile_cols * 2, 16);         // image tile
@@ -121,10 +122,7 @@ void choose_chunks(int K, int tile_cols, int *kc, int *nchunks) {
   *kc = best_c;
 }
 
-constexpr int kSmemPerSm = 228 * 1024;
-constexpr int kSmemPerCtaMax = 227 * 1024;
-
-}  // namespace
+}  // namespace dr
 
 extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires,
                              int32_t K, const double *edges, int32_t B,

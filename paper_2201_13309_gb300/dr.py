@@ -29,7 +29,8 @@ KERNELS = {0: "rows", 1: "pixels"}
 EXPORTS = ("dr_plan", "dr_plan_destroy", "dr_plan_get_info", "dr_plan_device_bytes",
            "dr_reconstruct", "dr_reconstruct_host", "dr_image_differences",
            "dr_plan_depths", "dr_plan_check", "dr_status_string", "dr_last_error",
-           "dr_version", "dr_reconstruct_rows_static")
+           "dr_version", "dr_reconstruct_rows_static", "dr_batch_create", "dr_batch_launch",
+           "dr_batch_check", "dr_batch_get_info", "dr_batch_destroy")
 
 _d3 = ctypes.c_double * 3
 
@@ -60,6 +61,22 @@ class PlanInfo(ctypes.Structure):
         d = {n: getattr(self, n) for n, _ in self._fields_}
         d["kernel"] = KERNELS.get(d["kernel"], d["kernel"])
         return d
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("d_images", ctypes.c_void_p),
+                ("d_out", ctypes.c_void_p)]
+
+
+class BatchOptions(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("max_tile_cols", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("scans", ctypes.c_int32), ("items", ctypes.c_int64), ("grid", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+                ("device_bytes", ctypes.c_size_t)]
 
 
 class DrError(RuntimeError):
@@ -97,6 +114,12 @@ def lib():
                 "dr_version": ([], ctypes.c_char_p),
                 "dr_reconstruct_rows_static": ([ctypes.POINTER(Geometry), P, I32, P, I32, P, P,
                                                 P, P], I32),
+                "dr_batch_create": ([ctypes.POINTER(Job), I32, ctypes.POINTER(BatchOptions),
+                                     ctypes.POINTER(P)], I32),
+                "dr_batch_launch": ([P, P], I32),
+                "dr_batch_check": ([P], I32),
+                "dr_batch_get_info": ([P, ctypes.POINTER(BatchInfo)], I32),
+                "dr_batch_destroy": ([P], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -230,6 +253,50 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().dr_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """dr_batch: several (plan, images, out) jobs reconstructed by one
+    persistent launch replayed from a CUDA graph.  The tensors are bound at
+    creation and must stay alive (and in place) while the batch exists."""
+
+    def __init__(self, jobs, ctas_per_sm=0, max_tile_cols=0):
+        self._keep = list(jobs)
+        self.ctas_per_sm = ctas_per_sm
+        arr = (Job * len(jobs))()
+        for i, (plan, images, out) in enumerate(jobs):
+            plan._check_shapes(images, out)
+            arr[i].plan = plan.handle
+            arr[i].d_images = images.data_ptr()
+            arr[i].d_out = out.data_ptr()
+        o = BatchOptions()
+        o.ctas_per_sm = int(ctas_per_sm)
+        o.max_tile_cols = int(max_tile_cols)
+        h = ctypes.c_void_p()
+        check(lib().dr_batch_create(arr, len(jobs), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        check(lib().dr_batch_launch(self._h, ctypes.c_void_p(_stream_handle(stream))))
+
+    def check_device(self):
+        check(lib().dr_batch_check(self._h))
+
+    def info(self):
+        i = BatchInfo()
+        check(lib().dr_batch_get_info(self._h, ctypes.byref(i)))
+        return {n: getattr(i, n) for n, _ in i._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().dr_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

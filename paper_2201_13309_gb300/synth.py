@@ -267,9 +267,9 @@ def spot_contributions(geom, wires, scat, spot_sigma=1.0):
         q = (np.asarray(geom["det_origin"])
              + rs[:, None, None] * np.asarray(geom["row_step"])
              + cs[None, :, None] * np.asarray(geom["col_step"]))
-        # [K, nr, nc]
-        vis = np.stack([~hidden_by_wire(src, q, wires[k], geom["wire_axis"],
-                                        geom["wire_radius"]) for k in kk])
+        # [K, nr, nc]: every wire step at once
+        vis = ~hidden_by_wire(src, q[None], wires[:, None, None, :], geom["wire_axis"],
+                              geom["wire_radius"])
         v = scat.peak[i] * prof[None] * vis
         flat = (kk[:, None, None] * H + rs[None, :, None]) * W + cs[None, None, :]
         idx.append(flat.reshape(-1))

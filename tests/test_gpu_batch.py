@@ -1,0 +1,123 @@
+"""Persistent batched launch (one kernel for many uneven scans, replayed from
+a CUDA graph) against the per-scan launches and the FP64 oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2201_13309_gb300 import dr, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def _dev(images):
+    return torch.from_numpy(np.ascontiguousarray(images).view(np.int16)).cuda()
+
+
+def _scans():
+    a = synth.tiny_scan(31, rows=40, cols=256, K=61)
+    b = synth.tiny_scan(32, rows=8, cols=512, K=301, n_scat=2)
+    b.edges = synth.bin_edges(-100.0, 320.0, 2.0)
+    c = synth.tiny_scan(33, rows=24, cols=64, K=37)
+    c.edges = synth.bin_edges(-30.0, 60.0, 0.5)
+    d = synth.tiny_scan(34, rows=16, cols=128, K=45)
+    d = synth.Scan(d.geom, d.wires[::-1].copy(), d.edges, d.images[::-1].copy())
+    return [(a, "leading"), (b, "leading"), (c, "trailing"), (d, "leading")]
+
+
+def test_batch_matches_per_scan_launches_bitwise():
+    jobs, refs, keep = [], [], []
+    for sc, edge in _scans():
+        plan = dr.Plan(sc.geom, sc.wires, sc.edges, edge=edge)
+        img = _dev(sc.images)
+        refs.append(plan.reconstruct(img))
+        out = torch.full_like(refs[-1], float("nan"))
+        jobs.append((plan, img, out))
+        keep.append((sc, edge))
+    batch = dr.Batch(jobs)
+    info = batch.info()
+    assert info["scans"] == 4 and info["threads"] == 512 and info["items"] > 0
+    batch.launch()
+    torch.cuda.synchronize()
+    batch.check_device()
+    for (plan, img, out), ref in zip(jobs, refs):
+        assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
+    # one against the oracle directly
+    sc, edge = keep[2]
+    got = jobs[2][2].cpu().numpy().astype(np.float64)
+    want = O.reconstruct(sc.geom, sc.wires, sc.images, sc.edges, edge)
+    s = np.abs(np.diff(sc.images.astype(np.int64), axis=0)).sum(0)[None]
+    assert np.all(np.abs(got - want) <= 1e-4 * s)
+
+
+@pytest.mark.parametrize("per_sm,cap", [(2, 0), (2, 64), (1, 32)])
+def test_batch_modes_agree(per_sm, cap):
+    jobs, refs = [], []
+    for sc, edge in _scans():
+        plan = dr.Plan(sc.geom, sc.wires, sc.edges, edge=edge)
+        img = _dev(sc.images)
+        refs.append(plan.reconstruct(img))
+        jobs.append((plan, img, torch.full_like(refs[-1], float("nan"))))
+    batch = dr.Batch(jobs, ctas_per_sm=per_sm, max_tile_cols=cap)
+    batch.launch()
+    torch.cuda.synchronize()
+    for (_, _, out), ref in zip(jobs, refs):
+        assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
+
+
+def test_batch_autotuner():
+    from paper_2201_13309_gb300 import autotune
+
+    jobs, refs = [], []
+    for sc, edge in _scans()[:2]:
+        plan = dr.Plan(sc.geom, sc.wires, sc.edges, edge=edge)
+        img = _dev(sc.images)
+        refs.append(plan.reconstruct(img))
+        jobs.append((plan, img, torch.empty_like(refs[-1])))
+    batch, tune = autotune.tuned_batch(jobs, reps=1)
+    assert len(tune["candidates"]) >= 2
+    batch.launch()
+    torch.cuda.synchronize()
+    for (_, _, out), ref in zip(jobs, refs):
+        assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
+
+
+def test_batch_replay_with_new_images():
+    sc, _ = _scans()[0]
+    plan = dr.Plan(sc.geom, sc.wires, sc.edges)
+    img = _dev(sc.images)
+    out = plan.empty_output()
+    batch = dr.Batch([(plan, img, out)])
+    batch.launch()
+    other = synth.tiny_scan(99, rows=40, cols=256, K=61).images
+    img.copy_(_dev(other))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    batch.launch(stream=s)
+    s.synchronize()
+    ref = plan.reconstruct(_dev(other))
+    torch.cuda.synchronize()
+    assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
+
+
+def test_batch_rejects_unsupported_jobs():
+    sc = synth.tiny_scan(35, rows=4, cols=64, K=9)
+    pix = dr.Plan(sc.geom, sc.wires, sc.edges, force_pixels=True)
+    img = _dev(sc.images)
+    with pytest.raises(dr.DrError) as ex:
+        dr.Batch([(pix, img, pix.empty_output())])
+    assert ex.value.status == 8
+    odd = synth.tiny_scan(36, rows=4, cols=12, K=9)
+    p2 = dr.Plan(odd.geom, odd.wires, odd.edges)
+    with pytest.raises(dr.DrError):
+        dr.Batch([(p2, _dev(odd.images), p2.empty_output())])
