@@ -211,6 +211,65 @@ dr_status dr_batch_check(dr_batch_t *batch);
 dr_status dr_batch_get_info(const dr_batch_t *batch, dr_batch_info *info);
 void dr_batch_destroy(dr_batch_t *batch);
 
+/* ---- Serving: a stream of requests ----------------------------------------
+ * A server takes reconstruction requests of any ROI, step and bin count as
+ * they arrive and runs them concurrently on one GPU (the paper's Sec. II names
+ * host<->device transfers as the cost to hide by overlapping them with
+ * computation; here each request's pinned-host upload overlaps other
+ * requests' kernels).  At creation the server reserves budget_bytes of device
+ * memory (one cudaMalloc) and starts a scheduler thread.  Requests are admitted
+ * in arrival order as soon as a slot (a stream) is free and their image and
+ * output blocks fit in the reserved memory; a request larger than the whole
+ * budget fails with DR_ERR_BUDGET.  Plans are cached by geometry, wire path
+ * and bins.  A request's image block is returned when its kernel finishes;
+ * its output stays on the device until dr_server_release.  Results are
+ * bitwise identical to dr_reconstruct's, alone or in any mix. */
+typedef struct dr_server dr_server_t;
+
+typedef struct {
+  size_t budget_bytes;        /* device memory for images + outputs */
+  int32_t slots;              /* requests on the GPU at once (streams); 0 = 4 */
+  int32_t plan_cache;         /* plans kept; 0 = 64 */
+  int32_t reserved[2];
+} dr_server_options;
+
+enum { DR_REQ_QUEUED = 0, DR_REQ_UPLOADING = 1, DR_REQ_RUNNING = 2, DR_REQ_DONE = 3,
+       DR_REQ_FAILED = 4 };
+
+/* Seconds since the server was created (host steady clock). */
+typedef struct {
+  double submitted, admitted, uploaded, done;
+} dr_request_times;
+
+typedef struct {
+  int64_t queued, in_flight, admitted, completed, failed, plans_built, plans_cached;
+  size_t arena_bytes, arena_used;
+} dr_server_stats;
+
+dr_status dr_server_create(const dr_server_options *options, dr_server_t **out);
+/* Queue one scan.  h_images [K][rows][cols] uint16 host memory (pinned for
+ * overlap) must stay valid and unchanged until the request is done.  The
+ * geometry, wire path and bins are copied. */
+dr_status dr_server_submit(dr_server_t *server, const dr_geometry *geometry,
+                           const double *wire_centres, int32_t K, const double *bin_edges,
+                           int32_t B, const uint16_t *h_images, uint64_t *id);
+/* Current state (DR_REQ_*) of a request. */
+dr_status dr_server_poll(dr_server_t *server, uint64_t id, int32_t *state);
+/* Block until the request is done or failed (DR_ERR_TIMEOUT after timeout_s). */
+dr_status dr_server_wait(dr_server_t *server, uint64_t id, double timeout_s);
+/* The device address of a done request's [B][rows][cols] FP32 output (valid
+ * until released) and its timestamps. */
+dr_status dr_server_fetch(dr_server_t *server, uint64_t id, const void **d_out,
+                          dr_request_times *times);
+/* Copy a done request's output into dst (device or host memory) on stream. */
+dr_status dr_server_fetch_into(dr_server_t *server, uint64_t id, void *dst,
+                               size_t dst_bytes, dr_stream_t stream);
+/* Give a done (or failed) request's output memory back and forget it. */
+dr_status dr_server_release(dr_server_t *server, uint64_t id);
+dr_status dr_server_get_stats(dr_server_t *server, dr_server_stats *stats);
+/* Stop the scheduler, wait for work in flight and free everything. */
+void dr_server_destroy(dr_server_t *server);
+
 /* ---- Reconstruction that allocates nothing -------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that
  * cannot call cudaMalloc themselves and so cannot build a plan (dr_plan keeps

@@ -117,6 +117,28 @@ dr_status dispatch_out(const dr_plan_t *p, bool tma, const CUtensorMap &tm, cons
 
 }  // namespace
 
+dr_status preload_kernels() {
+  const void *fns[] = {
+      (const void *)rows_kernel<GeoFx, float, true, 4>,
+      (const void *)rows_kernel<GeoFx, float, false, 4>,
+      (const void *)rows_kernel<GeoFx, float, true, 1>,
+      (const void *)rows_kernel<GeoFx, float, false, 1>,
+      (const void *)rows_kernel<GeoFx, __nv_bfloat16, true, 4>,
+      (const void *)rows_kernel<GeoFx, __nv_bfloat16, false, 4>,
+      (const void *)rows_kernel<GeoFx, __nv_bfloat16, true, 1>,
+      (const void *)rows_kernel<GeoFx, __nv_bfloat16, false, 1>,
+      (const void *)pixels_kernel<GeoFx, float, true>,
+      (const void *)pixels_kernel<GeoFx, float, false>,
+      (const void *)pixels_kernel<GeoFx, __nv_bfloat16, true>,
+      (const void *)pixels_kernel<GeoFx, __nv_bfloat16, false>,
+  };
+  for (const void *f : fns) {
+    dr_status s = allow_smem(f);
+    if (s != DR_OK) return s;
+  }
+  return DR_OK;
+}
+
 // Build the [K][rows][cols] uint16 tensor map with a [kc][1][tile_cols] box.
 dr_status make_tensor_map(const dr_plan_t *p, const uint16_t *img, CUtensorMap *tm) {
   auto enc = encoder();

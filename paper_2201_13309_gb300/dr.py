@@ -30,7 +30,11 @@ EXPORTS = ("dr_plan", "dr_plan_destroy", "dr_plan_get_info", "dr_plan_device_byt
            "dr_reconstruct", "dr_reconstruct_host", "dr_image_differences",
            "dr_plan_depths", "dr_plan_check", "dr_status_string", "dr_last_error",
            "dr_version", "dr_reconstruct_rows_static", "dr_batch_create", "dr_batch_launch",
-           "dr_batch_check", "dr_batch_get_info", "dr_batch_destroy")
+           "dr_batch_check", "dr_batch_get_info", "dr_batch_destroy", "dr_server_create",
+           "dr_server_submit", "dr_server_poll", "dr_server_wait", "dr_server_fetch",
+           "dr_server_fetch_into", "dr_server_release", "dr_server_get_stats",
+           "dr_server_destroy")
+REQ_STATES = {0: "queued", 1: "uploading", 2: "running", 3: "done", 4: "failed"}
 
 _d3 = ctypes.c_double * 3
 
@@ -79,6 +83,22 @@ class BatchInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t)]
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("slots", ctypes.c_int32),
+                ("plan_cache", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+class RequestTimes(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_double), ("admitted", ctypes.c_double),
+                ("uploaded", ctypes.c_double), ("done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("queued", "in_flight", "admitted", "completed",
+                                               "failed", "plans_built", "plans_cached")] + [
+        ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t)]
+
+
 class DrError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -120,6 +140,17 @@ def lib():
                 "dr_batch_check": ([P], I32),
                 "dr_batch_get_info": ([P, ctypes.POINTER(BatchInfo)], I32),
                 "dr_batch_destroy": ([P], None),
+                "dr_server_create": ([ctypes.POINTER(ServerOptions), ctypes.POINTER(P)], I32),
+                "dr_server_submit": ([P, ctypes.POINTER(Geometry), P, I32, P, I32, P,
+                                      ctypes.POINTER(ctypes.c_uint64)], I32),
+                "dr_server_poll": ([P, ctypes.c_uint64, ctypes.POINTER(I32)], I32),
+                "dr_server_wait": ([P, ctypes.c_uint64, ctypes.c_double], I32),
+                "dr_server_fetch": ([P, ctypes.c_uint64, ctypes.POINTER(P),
+                                     ctypes.POINTER(RequestTimes)], I32),
+                "dr_server_fetch_into": ([P, ctypes.c_uint64, P, SZ, P], I32),
+                "dr_server_release": ([P, ctypes.c_uint64], I32),
+                "dr_server_get_stats": ([P, ctypes.POINTER(ServerStats)], I32),
+                "dr_server_destroy": ([P], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -298,6 +329,76 @@ class Batch:
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().dr_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """dr_server: continuous admission of reconstruction requests against a
+    device-memory budget; results stay on the device until released."""
+
+    def __init__(self, budget_bytes, slots=0, plan_cache=0):
+        o = ServerOptions()
+        o.budget_bytes = int(budget_bytes)
+        o.slots = int(slots)
+        o.plan_cache = int(plan_cache)
+        h = ctypes.c_void_p()
+        check(lib().dr_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._pinned = {}
+
+    def submit(self, geom, wires, edges, h_images, edge="leading"):
+        """h_images: host (pinned) 16-bit tensor [K, rows, cols]; kept alive
+        by the server object until the request is released."""
+        w = np.ascontiguousarray(wires, dtype=np.float64)
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        g = geometry_struct(geom, edge)
+        rid = ctypes.c_uint64()
+        check(lib().dr_server_submit(self._h, ctypes.byref(g), w.ctypes.data_as(ctypes.c_void_p),
+                                     w.shape[0], e.ctypes.data_as(ctypes.c_void_p),
+                                     e.shape[0] - 1, _dptr(h_images), ctypes.byref(rid)))
+        self._pinned[rid.value] = h_images
+        return rid.value
+
+    def poll(self, rid):
+        st = ctypes.c_int32()
+        check(lib().dr_server_poll(self._h, rid, ctypes.byref(st)))
+        return REQ_STATES[st.value]
+
+    def wait(self, rid, timeout=600.0):
+        check(lib().dr_server_wait(self._h, rid, float(timeout)))
+
+    def fetch(self, rid):
+        """(device address of the output, timestamps in s since creation)."""
+        p = ctypes.c_void_p()
+        t = RequestTimes()
+        check(lib().dr_server_fetch(self._h, rid, ctypes.byref(p), ctypes.byref(t)))
+        return p.value, {n: getattr(t, n) for n, _ in t._fields_}
+
+    def fetch_into(self, rid, dst, stream=None):
+        check(lib().dr_server_fetch_into(self._h, rid, _dptr(dst),
+                                         dst.numel() * dst.element_size(),
+                                         ctypes.c_void_p(_stream_handle(stream))))
+        return dst
+
+    def release(self, rid):
+        check(lib().dr_server_release(self._h, rid))
+        self._pinned.pop(rid, None)
+
+    def stats(self):
+        s = ServerStats()
+        check(lib().dr_server_get_stats(self._h, ctypes.byref(s)))
+        return {n: getattr(s, n) for n, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().dr_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._pinned.clear()
 
     def __del__(self):
         try:
