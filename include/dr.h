@@ -145,6 +145,21 @@ dr_status dr_reconstruct_host(const dr_plan_t *plan, const uint16_t *h_images,
                               void *h_out, uint16_t *d_images_ws,
                               void *d_out_ws, dr_stream_t stream);
 
+/* Streamed (out-of-core) form, the row-slab chunking of the paper's Sec. III-B
+ * with the transfer overlap its Sec. II motivates: the scan moves through a
+ * device workspace of ws_bytes (256-byte aligned) in slabs of slab_rows rows
+ * (0 = as large as three slab buffers allow).  For each slab: one 2-D
+ * host->device copy of its rows of every image, the reconstruction kernel,
+ * and one 2-D device->host copy of its rows of every bin; three internal
+ * streams overlap uploads, kernels and downloads across slabs.  h_images
+ * [K][rows][cols] and h_out [B][rows][cols] are host memory (pinned for full
+ * speed).  Ordered after prior work on stream; later work on stream waits
+ * for the last download.  Calls are serialised by the library (one internal
+ * stream set per device).  DR_ERR_BUDGET if three slabs do not fit. */
+dr_status dr_reconstruct_streamed(const dr_plan_t *plan, const uint16_t *h_images,
+                                  void *h_out, void *d_workspace, size_t workspace_bytes,
+                                  int32_t slab_rows, dr_stream_t stream);
+
 /* The exact integer differences the kernels use (Sec. III-C "difference
  * intensity at each pixel"): d_diff[k][p] = images[k][p] - images[k+1][p] as
  * int32, k = 0..K-2, for a [K][rows][cols] uint16 device stack. */

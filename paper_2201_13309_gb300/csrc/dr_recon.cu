@@ -384,3 +384,130 @@ extern "C" dr_status dr_reconstruct_rows_static(const dr_geometry *g, const doub
   if (e != cudaSuccess) return cuda_fail("dr_reconstruct_rows_static: launch", e);
   return DR_OK;
 }
+
+// ------------------------------------------- streamed (out-of-core) form ---
+// Row slabs of the scan flow through a small device workspace: host->device
+// copy of a slab of every image (one 2-D copy: K planes, each slab_rows x cols
+// uint16 at a pitch of rows x cols), the kernel on that slab, and a 2-D copy
+// of the slab's bins back to the host.  Three streams overlap the two copy
+// directions with the kernels; nbuf slab buffers rotate.  Used when the scan
+// does not fit in device memory, and for the end-to-end form.
+
+namespace {
+
+struct StreamSet {
+  cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
+  cudaEvent_t start = nullptr, up_done[3] = {}, comp_done[3] = {}, down_done[3] = {};
+  bool ok = false;
+};
+std::mutex g_streamset_mu;
+StreamSet g_streamsets[64];
+
+dr_status stream_set(StreamSet **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+  if (dev < 0 || dev >= 64) {
+    set_error("device %d out of range", dev);
+    return DR_ERR_UNSUPPORTED;
+  }
+  StreamSet &s = g_streamsets[dev];
+  if (!s.ok) {
+    const unsigned ev = cudaEventDisableTiming;
+    e = cudaStreamCreateWithFlags(&s.up, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.comp, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.down, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.start, ev);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+      e = cudaEventCreateWithFlags(&s.up_done[i], ev);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.comp_done[i], ev);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.down_done[i], ev);
+    }
+    if (e != cudaSuccess) return cuda_fail("stream set", e);
+    s.ok = true;
+  }
+  *out = &s;
+  return DR_OK;
+}
+
+}  // namespace
+
+extern "C" dr_status dr_reconstruct_streamed(const dr_plan_t *p, const uint16_t *h_img,
+                                             void *h_out, void *d_ws, size_t ws_bytes,
+                                             int32_t slab_rows, dr_stream_t stream) {
+  if (!p) {
+    set_error("dr_reconstruct_streamed: null plan");
+    return DR_ERR_INVALID_ARG;
+  }
+  const int H = p->rows, W = p->cols, K = p->K, B = p->B;
+  if ((size_t)H * W == 0) return DR_OK;
+  if (!h_img || !h_out || !d_ws) {
+    set_error("dr_reconstruct_streamed: null buffer");
+    return DR_ERR_INVALID_ARG;
+  }
+  const size_t osz = p->out_dtype == DR_OUT_BF16 ? 2 : 4;
+  auto slab_bytes = [&](int n) {
+    return ((size_t)n * W * K * 2 + 255) / 256 * 256 + ((size_t)n * W * B * osz + 255) / 256 * 256;
+  };
+  const int nbuf = 3;
+  if (slab_rows <= 0) {  // largest slab with three buffers in the workspace
+    slab_rows = (int)std::min<size_t>(H, ws_bytes / nbuf / std::max<size_t>(slab_bytes(1), 1));
+    if (slab_rows > 64) slab_rows = slab_rows / 8 * 8;
+  }
+  slab_rows = std::min(slab_rows, H);
+  if (slab_rows < 1 || slab_bytes(slab_rows) * nbuf > ws_bytes || ((uintptr_t)d_ws & 255)) {
+    set_error("dr_reconstruct_streamed: workspace of %zu bytes holds no three slabs of %d rows "
+              "(%zu bytes each, 256-byte aligned)", ws_bytes, slab_rows, slab_bytes(std::max(slab_rows, 1)));
+    return DR_ERR_BUDGET;
+  }
+  StreamSet *ss = nullptr;
+  std::lock_guard<std::mutex> lk(g_streamset_mu);
+  dr_status s = stream_set(&ss);
+  if (s != DR_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaEventRecord(ss->start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->up, ss->start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->comp, ss->start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->down, ss->start, 0);
+  if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: fork", e);
+  const int groups_per_row = p->kernel == DR_KERNEL_ROWS ? 1 : W;
+  const int nslab = (H + slab_rows - 1) / slab_rows;
+  for (int i = 0; i < nslab; ++i) {
+    const int b = i % nbuf, r0 = i * slab_rows, n = std::min(slab_rows, H - r0);
+    unsigned char *buf = static_cast<unsigned char *>(d_ws) + slab_bytes(slab_rows) * b;
+    uint16_t *dimg = reinterpret_cast<uint16_t *>(buf);
+    void *dout = buf + ((size_t)slab_rows * W * K * 2 + 255) / 256 * 256;
+    // upload: wait until the kernel that last read this buffer is done
+    if (i >= nbuf) e = cudaStreamWaitEvent(ss->up, ss->comp_done[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(dimg, (size_t)n * W * 2, h_img + (size_t)r0 * W, (size_t)H * W * 2,
+                            (size_t)n * W * 2, K, cudaMemcpyHostToDevice, ss->up);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->up_done[b], ss->up);
+    // kernel: after the upload, and after the previous download of this buffer
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->comp, ss->up_done[b], 0);
+    if (e == cudaSuccess && i >= nbuf) e = cudaStreamWaitEvent(ss->comp, ss->down_done[b], 0);
+    if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: upload", e);
+    dr_plan_t slab = *p;
+    slab.rows = n;
+    slab.c.H = n;
+    slab.c.grp = p->c.grp + (size_t)r0 * groups_per_row;
+    slab.c.grp64 = p->c.grp64 + (size_t)r0 * groups_per_row;
+    s = launch_reconstruct(&slab, dimg, dout, ss->comp);
+    if (s != DR_OK) return s;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(ss->comp_done[b], ss->comp);
+    // download the slab's bins into rows r0.. of every output plane
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->down, ss->comp_done[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(static_cast<unsigned char *>(h_out) + (size_t)r0 * W * osz,
+                            (size_t)H * W * osz, dout, (size_t)n * W * osz, (size_t)n * W * osz, B,
+                            cudaMemcpyDeviceToHost, ss->down);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->down_done[b], ss->down);
+    if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: download", e);
+  }
+  // join: the caller's stream continues after the last download
+  e = cudaEventRecord(ss->down_done[0], ss->down);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ss->down_done[0], 0);
+  if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: join", e);
+  return DR_OK;
+}

@@ -33,7 +33,7 @@ EXPORTS = ("dr_plan", "dr_plan_destroy", "dr_plan_get_info", "dr_plan_device_byt
            "dr_batch_check", "dr_batch_get_info", "dr_batch_destroy", "dr_server_create",
            "dr_server_submit", "dr_server_poll", "dr_server_wait", "dr_server_fetch",
            "dr_server_fetch_into", "dr_server_release", "dr_server_get_stats",
-           "dr_server_destroy")
+           "dr_server_destroy", "dr_reconstruct_streamed")
 REQ_STATES = {0: "queued", 1: "uploading", 2: "running", 3: "done", 4: "failed"}
 
 _d3 = ctypes.c_double * 3
@@ -151,6 +151,7 @@ def lib():
                 "dr_server_release": ([P, ctypes.c_uint64], I32),
                 "dr_server_get_stats": ([P, ctypes.POINTER(ServerStats)], I32),
                 "dr_server_destroy": ([P], None),
+                "dr_reconstruct_streamed": ([P, P, P, P, SZ, I32, P], I32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -257,6 +258,19 @@ class Plan:
         check(lib().dr_reconstruct_host(self._h, _dptr(h_images), _dptr(h_out),
                                         _dptr(d_images), _dptr(d_out),
                                         ctypes.c_void_p(_stream_handle(stream))))
+        return h_out
+
+    def reconstruct_streamed(self, h_images, h_out, workspace, slab_rows=0, stream=None):
+        """Out-of-core form: host images -> row slabs through a device
+        workspace (a CUDA tensor; three slab buffers) -> host output."""
+        if tuple(h_images.shape) != (self.K, self.rows, self.cols):
+            raise ValueError("h_images shape")
+        if tuple(h_out.shape) != (self.B, self.rows, self.cols):
+            raise ValueError("h_out shape")
+        check(lib().dr_reconstruct_streamed(
+            self._h, _dptr(h_images), _dptr(h_out), _dptr(workspace),
+            workspace.numel() * workspace.element_size(), int(slab_rows),
+            ctypes.c_void_p(_stream_handle(stream))))
         return h_out
 
     def depths(self, r0=0, nrows=None, stream=None):
