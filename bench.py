@@ -149,6 +149,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def reduce_max(x, device):
+    """Max of a float over all ranks (the slowest rank's time); identity on
+    one process."""
+    import torch
+    import torch.distributed as tdist
+
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, max_ms):
+    """Units all ranks processed per second, timed by the slowest rank."""
+    return world * units_per_rank_step * steps / (max_ms * 1e-3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -649,13 +667,9 @@ def main():
         stop.synchronize()
     barrier()
     plan.check_device()
-    elapsed_ms = start.elapsed_time(stop)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = reduce_max(start.elapsed_time(stop), dev)
     ms_per_step = elapsed_ms / args.steps
-    value = world * units_per_step * args.steps / (elapsed_ms * 1e-3)
+    value = whole_job_rate(units_per_step, args.steps, world, elapsed_ms)
 
     # kernel roofline: one launch per step, so the event time per step is
     # the kernel's average launch duration
@@ -692,18 +706,13 @@ def main():
             e1.record(stream)
             e1.synchronize()
             barrier()
-            ms = e0.elapsed_time(e1)
-            if world > 1:
-                t = torch.tensor([ms], device=dev)
-                tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-                ms = float(t.item())
-            return ms
+            return reduce_max(e0.elapsed_time(e1), dev)
 
         e2e_ms = timed(lambda: plan.reconstruct_streamed(h_img, h_out, ws, slab_rows=slab,
                                                          stream=stream), args.e2e_steps)
         serial_ms = timed(lambda: plan.reconstruct_host(h_img, h_out, images, out, stream=stream),
                           args.e2e_steps)
-        e2e = {"value": world * units_per_step * args.e2e_steps / (e2e_ms * 1e-3), "unit": UNIT,
+        e2e = {"value": whole_job_rate(units_per_step, args.e2e_steps, world, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(images.numel() * 2),
                "d2h_bytes_per_step": int(out.numel() * out.element_size()),
                "steps": args.e2e_steps, "ms_per_step": e2e_ms / args.e2e_steps,
