@@ -101,6 +101,8 @@ typedef struct {
   int32_t out_dtype, geom_precision, edge, reversed;
   int32_t fixed_shift;      /* depth positions in units of 2^-fixed_shift mm
                                of projected depth (FP32 geometry) */
+  int32_t row_tables;       /* 1: the per-row (k, f) tables were built once at
+                               plan time; 0: each tile builds its own */
   double depth_min, depth_max;   /* range of all d_k (mm) */
   double min_step;               /* smallest |d_{k+1} - d_k| (mm) */
   size_t device_bytes;           /* device memory held by the plan */

@@ -56,6 +56,15 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load_1d(void *dst, const void *src, uint32_t bytes,
+                                             uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Wait for the TMA phase with a time limit.  On timeout the error word is
 // set, the copies in flight get a second bounded wait to land, and the caller
 // returns without touching the tile.
@@ -265,6 +274,60 @@ __device__ __forceinline__ void stage_tile(const CUtensorMap *tmap, const uint16
 // the persistent kernel's work slot; then the image tile [Kpad][tile_cols]
 // uint16, the row's depth positions [K], and the (k, f) table [B + 1].
 
+// The row's (k_j, f_j) table: depth positions of the row into spos (smem,
+// K entries), then for every bin edge j: k = last step below the edge
+// (clamped to an interval), f = position of the edge inside [d_k, d_{k+1}]
+// (clamped), written to out1[j].  Edges at or below d_0 give F = 0 and edges
+// at or above d_{K-1} give F = S_{K-1}, so only bins [nz_lo, nz_hi) can hold
+// data.  zcount (2 ints, smem) must be zero before the first barrier here.
+// Contains two __syncthreads; every thread of the CTA must call it.
+template <class Geo>
+__device__ __forceinline__ int2 build_row_table(const Consts &c, int row,
+                                                typename Geo::pos_t *spos, int2 *out1,
+                                                int *zcount) {
+  using pos_t = typename Geo::pos_t;
+  const int K = c.K, B = c.B, tid = threadIdx.x, NT = blockDim.x;
+  const auto &g = Geo::group(c, row);
+  const auto *steps = Geo::steps(c);
+  for (int k = tid; k < K; k += NT) spos[k] = Geo::depth(g, steps[k], c);
+  __syncthreads();
+  int below = 0, above = 0;
+  const pos_t tfirst = spos[0], tlast = spos[K - 1];
+  for (int j = tid; j <= B; j += NT) {
+    const pos_t e = Geo::edge(c, j);
+    int lo = 0, hi = K;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (spos[mid] < e) lo = mid + 1; else hi = mid;
+    }
+    const int k = min(max(lo - 1, 0), K - 2);
+    const float f = Geo::frac(e, spos[k], Geo::inv_len(spos[k], spos[k + 1]));
+    out1[j] = make_int2(k, __float_as_int(f));
+    below += !(e > tfirst);
+    above += !(e < tlast);
+  }
+  if (below) atomicAdd(&zcount[0], below);
+  if (above) atomicAdd(&zcount[1], above);
+  __syncthreads();
+  const int nz_hi = min(B + 1 - zcount[1], B);
+  const int nz_lo = min(max(zcount[0] - 1, 0), nz_hi);
+  return make_int2(nz_lo, nz_hi);
+}
+
+// Plan-time tables: one CTA per row writes its header and edge entries.
+template <class Geo>
+__global__ void __launch_bounds__(256) tables_kernel(const Consts c, int2 *tab) {
+  extern __shared__ __align__(16) unsigned char tsmem[];
+  int *zcount = reinterpret_cast<int *>(tsmem);
+  auto *spos = reinterpret_cast<typename Geo::pos_t *>(tsmem + 16);
+  const int row = blockIdx.x;
+  if (threadIdx.x == 0) zcount[0] = zcount[1] = 0;
+  int2 *trow = tab + (size_t)row * c.tab_stride;
+  const int2 nz = build_row_table<Geo>(c, row, spos, trow + 1, zcount);
+  if (threadIdx.x == 0) trow[0] = nz;
+  for (int i = c.B + 2 + threadIdx.x; i < c.tab_stride; i += blockDim.x) trow[i] = make_int2(0, 0);
+}
+
 // One tile: row `row`, columns c0 .. c0 + tile_cols - 1, all steps and bins.
 // The mbarrier at smem[0] must be initialised; `parity` is its phase for this
 // tile.  Returns false (for every thread of the CTA) if the bounded TMA wait
@@ -281,45 +344,40 @@ __device__ __forceinline__ bool rows_tile(const CUtensorMap *tmap, const uint16_
   const int TC = t.tile_cols, K = c.K, B = c.B;
   const int Kpad = t.kc * t.nchunks;
   pos_t *spos = reinterpret_cast<pos_t *>(smem + 128 + align16((size_t)Kpad * TC * 2));
-  int2 *stab = reinterpret_cast<int2 *>(reinterpret_cast<unsigned char *>(spos) +
-                                        align16((size_t)K * sizeof(pos_t)));
+  int2 *stab0 = reinterpret_cast<int2 *>(reinterpret_cast<unsigned char *>(spos) +
+                                         align16((size_t)K * sizeof(pos_t)));
+  int2 *stab = stab0 + 1;  // stab[j], j = 0..B
   const int tid = threadIdx.x, NT = blockDim.x;
+  const bool pre = c.tab != nullptr;
+  const int2 *grow = pre ? c.tab + (size_t)row * c.tab_stride : nullptr;
 
-  stage_tile<kTma>(tmap, img, simg, bar, c, t, row, c0);
-  if (tid == 0) zcount[0] = zcount[1] = 0;
-  // depth positions of this row (processing order: increasing depth)
-  const auto &g = Geo::group(c, row);
-  const auto *steps = Geo::steps(c);
-  for (int k = tid; k < K; k += NT) spos[k] = Geo::depth(g, steps[k], c);
-  __syncthreads();
-  // each bin edge -> (k, f): k = last step below the edge (clamped to an
-  // interval), f = position of the edge inside [d_k, d_{k+1}], clamped.
-  // Edges at or below d_0 give F = 0 and edges at or above d_{K-1} give
-  // F = S_{K-1}, so only bins [nz_lo, nz_hi) can hold data.
-  int below = 0, above = 0;
-  const pos_t tfirst = spos[0], tlast = spos[K - 1];
-  for (int j = tid; j <= B; j += NT) {
-    const pos_t e = Geo::edge(c, j);
-    int lo = 0, hi = K;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (spos[mid] < e) lo = mid + 1; else hi = mid;
+  // images (and the plan's row table) into shared memory
+  if constexpr (kTma) {
+    if (tid == 0) {
+      const uint32_t tab_bytes = pre ? (uint32_t)c.tab_stride * 8u : 0u;
+      mbar_expect_tx(bar, (uint32_t)(t.kc * t.nchunks * TC * 2) + tab_bytes);
+      for (int ch = 0; ch < t.nchunks; ++ch)
+        tma_load_3d(simg + (size_t)ch * t.kc * TC, tmap, bar, c0, row, ch * t.kc);
+      if (pre) bulk_load_1d(stab0, grow, tab_bytes, bar);
     }
-    const int k = min(max(lo - 1, 0), K - 2);
-    const float f = Geo::frac(e, spos[k], Geo::inv_len(spos[k], spos[k + 1]));
-    stab[j] = make_int2(k, __float_as_int(f));
-    below += !(e > tfirst);
-    above += !(e < tlast);
+  } else {
+    stage_tile<false>(tmap, img, simg, bar, c, t, row, c0);
+    if (pre)
+      for (int i = tid; i < c.tab_stride; i += NT) stab0[i] = grow[i];
   }
-  if (below) atomicAdd(&zcount[0], below);
-  if (above) atomicAdd(&zcount[1], above);
-  __syncthreads();
-  const int nz_hi = min(B + 1 - zcount[1], B);
-  const int nz_lo = min(max(zcount[0] - 1, 0), nz_hi);
+  int2 nz;
+  if (!pre) {
+    if (tid == 0) zcount[0] = zcount[1] = 0;
+    nz = build_row_table<Geo>(c, row, spos, stab, zcount);
+  }
   if constexpr (kTma) {
     const bool late = !mbar_wait_bounded(bar, parity, c.err);
     if (__syncthreads_or(late)) return false;
+  } else {
+    if (pre) __syncthreads();
   }
+  if (pre) nz = stab0[0];
+  const int nz_lo = nz.x, nz_hi = nz.y;
 
   // stream the bins; thread = PPT adjacent pixels; the zero ranges and the
   // data range are each split evenly over the bin groups
@@ -384,7 +442,10 @@ __global__ void __launch_bounds__(512) rows_kernel(const __grid_constant__ CUten
                                                    const Tuning t) {
   extern __shared__ __align__(128) unsigned char smem[];
   if constexpr (kTma) {
+    // every thread waits on this barrier: make its initialisation visible
+    // to the CTA before any thread can poll it
     if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
+    __syncthreads();
   }
   rows_tile<Geo, OutT, kTma, PPT>(&tmap, img, out, c, t, blockIdx.y, blockIdx.x * t.tile_cols,
                                   smem, 0u);

@@ -54,6 +54,9 @@ void choose_chunks(int K, int tile_cols, int *kc, int *nchunks);
 dr_status allow_smem(const void *fn);
 // [K][rows][cols] uint16 tensor map with a [kc][1][tile_cols] box (p->tune).
 dr_status make_tensor_map(const dr_plan_t *p, const uint16_t *img, CUtensorMap *tm);
+// Build the plan's per-row (k, f) tables into tab (H rows of c.tab_stride
+// entries) on the device; synchronous.
+dr_status build_plan_tables(const dr_plan_t *p, int2 *tab);
 // Load every reconstruction kernel on the current device (module loading is
 // otherwise lazy, at the first launch).
 dr_status preload_kernels();

@@ -83,7 +83,7 @@ int rows_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64) {
   size_t s = 128;                                          // mbarrier slot
   s += align_up((size_t)Kpad * tile_cols * 2, 16);         // image tile
   s += align_up((size_t)K * (f64 ? 8 : 4), 16);            // depth positions
-  s += align_up((size_t)(B + 1) * 8, 16);                  // (k, f) table
+  s += align_up((size_t)row_table_entries(B) * 8, 16);     // header + (k, f) table
   return (int)s;
 }
 
@@ -473,6 +473,12 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires,
   size_t o_efx = take(sizeof(int32_t) * (B + 1)), o_gd = take(sizeof(GroupD) * G);
   size_t o_sd = take(sizeof(StepD) * K), o_e64 = take(sizeof(double) * (B + 1));
   size_t o_err = take(sizeof(int32_t) * 4);
+  // per-row (k, f) tables, built once on the device below (rows kernel only;
+  // above 1 GiB the tiles build their own)
+  const int tab_stride = row_table_entries(B);
+  const size_t tab_bytes = (size_t)H * tab_stride * 8;
+  const bool row_tables = rows_shared && H > 0 && W > 0 && tab_bytes <= (size_t(1) << 30);
+  size_t o_tab = row_tables ? take(tab_bytes) : 0;
   size_t total = align_up(off, 256);
   void *blk = nullptr;
   cudaError_t ce = cudaMalloc(&blk, total);
@@ -524,6 +530,16 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires,
   c.nb = nb;
   // trailing edge: the reverse change; reversed step order: negated sweep
   c.out_sign = (float)((g->edge == DR_EDGE_LEADING ? 1.0 : -1.0) * (reverse ? -1.0 : 1.0));
+  c.tab = nullptr;
+  c.tab_stride = tab_stride;
+  if (row_tables) {
+    dr_status st = build_plan_tables(p, reinterpret_cast<int2 *>(b + o_tab));
+    if (st != DR_OK) {
+      dr_plan_destroy(p);
+      return st;
+    }
+    c.tab = reinterpret_cast<const int2 *>(b + o_tab);
+  }
   *out = p;
   return DR_OK;
 }
@@ -559,6 +575,7 @@ extern "C" dr_status dr_plan_get_info(const dr_plan_t *p, dr_plan_info *info) {
   info->edge = p->edge;
   info->reversed = p->c.reverse;
   info->fixed_shift = p->shift;
+  info->row_tables = p->c.tab != nullptr;
   info->depth_min = p->depth_min;
   info->depth_max = p->depth_max;
   info->min_step = p->min_step;

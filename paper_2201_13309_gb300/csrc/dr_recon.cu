@@ -117,6 +117,27 @@ dr_status dispatch_out(const dr_plan_t *p, bool tma, const CUtensorMap &tm, cons
 
 }  // namespace
 
+dr_status build_plan_tables(const dr_plan_t *p, int2 *tab) {
+  const bool f64 = p->geom_prec == DR_GEOM_FP64;
+  const size_t smem = 16 + (size_t)p->K * (f64 ? 8 : 4);
+  const void *fn = f64 ? (const void *)tables_kernel<GeoF64> : (const void *)tables_kernel<GeoFx>;
+  dr_status s = allow_smem(fn);
+  if (s != DR_OK) return s;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail("plan tables: stream", e);
+  if (f64)
+    tables_kernel<GeoF64><<<p->rows, 256, smem, st>>>(p->c, tab);
+  else
+    tables_kernel<GeoFx><<<p->rows, 256, smem, st>>>(p->c, tab);
+  e = cudaGetLastError();
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail("plan tables", e);
+  return DR_OK;
+}
+
 dr_status preload_kernels() {
   const void *fns[] = {
       (const void *)rows_kernel<GeoFx, float, true, 4>,
@@ -492,6 +513,7 @@ extern "C" dr_status dr_reconstruct_streamed(const dr_plan_t *p, const uint16_t 
     slab.c.H = n;
     slab.c.grp = p->c.grp + (size_t)r0 * groups_per_row;
     slab.c.grp64 = p->c.grp64 + (size_t)r0 * groups_per_row;
+    if (p->c.tab) slab.c.tab = p->c.tab + (size_t)r0 * p->c.tab_stride;
     s = launch_reconstruct(&slab, dimg, dout, ss->comp);
     if (s != DR_OK) return s;
     e = cudaGetLastError();

@@ -71,7 +71,17 @@ struct Consts {
   double nb;               // |projected unit beam direction|: d = t / nb
   float out_sign;          // +1 leading/forward; -1 trailing or reversed
   int32_t *err;            // device error word
+  // Per-row tables built once by the plan (null: each tile builds its own):
+  // row r holds tab_stride int2 entries at tab + r * tab_stride, [0] =
+  // (first, end) of the bins that can hold data, [1 + j] = (k_j, f_j bits)
+  // for edge j = 0..B.
+  const int2 *tab;
+  int tab_stride;
 };
+
+// Entries of one row table: a header, B + 1 edges, rounded up to an even
+// count so that a row is a multiple of 16 bytes (bulk-copy granule).
+__host__ __device__ inline int row_table_entries(int B) { return (B + 2 + 1) & ~1; }
 
 // Error codes written to the device error word.
 enum : int32_t { kDevOk = 0, kDevTmaTimeout = 1 };

@@ -56,7 +56,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "rows", "cols", "K", "B", "kernel", "tile_cols", "pixels_per_thread",
         "bin_groups", "threads", "smem_bytes", "tma_chunk", "tma_chunks", "out_dtype",
-        "geom_precision", "edge", "reversed", "fixed_shift")] + [
+        "geom_precision", "edge", "reversed", "fixed_shift", "row_tables")] + [
         ("depth_min", ctypes.c_double), ("depth_max", ctypes.c_double),
         ("min_step", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
         ("bytes_per_call", ctypes.c_double)]

@@ -65,6 +65,7 @@ def test_tiny_scan_rows_kernel():
     plan, out = run(sc)
     info = plan.info()
     assert info["kernel"] == "rows" and info["pixels_per_thread"] == 4
+    assert info["row_tables"] == 1
     assert_parity(out.cpu().numpy(), ref_of(sc), sc.images)
 
 
