@@ -341,14 +341,27 @@ def batch_waves(specs, budget_bytes):
     return waves
 
 
-def run_batched(args, dev):
-    """64 uneven scans: per-scan launch loop vs one persistent launch per wave
+def small_roi_spec(seed):
+    """A scan of the uneven-batch distribution restricted to small ROIs
+    (256^2 or 512^2), where launch tails dominate a per-scan loop."""
+    from paper_2201_13309_gb300 import synth
+
+    for s in range(seed * 1000, seed * 1000 + 1000):
+        sp = synth.batch_scan_spec(s)
+        if sp.geom["rows"] <= 512:
+            return sp
+    raise RuntimeError("no small ROI found")
+
+
+def run_batched(args, dev, specs=None):
+    """Uneven scans: per-scan launch loop vs one persistent launch per wave
     (replayed from a captured CUDA graph), same plans, same buffers."""
     import torch
 
     from paper_2201_13309_gb300 import autotune, dr, synth
 
-    specs = [synth.batch_scan_spec(s) for s in range(args.batch_scans)]
+    if specs is None:
+        specs = [synth.batch_scan_spec(s) for s in range(args.batch_scans)]
     waves = batch_waves(specs, args.budget_gb * 1e9)
     tot_loop = tot_batch = 0.0
     units = bytes_alg = 0.0
@@ -403,7 +416,7 @@ def run_batched(args, dev):
         tot_batch += t_batch
         per_wave.append({"scans": len(wave), "loop_ms": t_loop, "batch_ms": t_batch,
                          "items": batch.info()["items"], "ctas_per_sm": btune["ctas_per_sm"],
-                         "max_tile_cols": btune["max_tile_cols"]})
+                         "max_tile_cols": btune["max_tile_cols"], "threads": btune["threads"]})
         batch.close()
         for plan, img, out in jobs:
             plan.close()
@@ -605,7 +618,13 @@ def main():
 
     if args.mode == "batched":
         if rank == 0:
-            print(json.dumps(run_batched(args, dev)), flush=True)
+            res = run_batched(args, dev)
+            small = run_batched(args, dev, [small_roi_spec(s) for s in range(args.batch_scans)])
+            res["small_roi_mix"] = {k: small[k] for k in ("scans", "waves", "loop", "batch",
+                                                          "speedup", "bitwise_equal")}
+            res["small_roi_mix"]["workload"] = ("64 scans of the same distribution restricted "
+                                                "to 256^2 and 512^2 ROIs")
+            print(json.dumps(res), flush=True)
         return 0
     if args.mode == "served":
         if rank == 0:

@@ -205,7 +205,8 @@ typedef struct {
                                  CTA) or 2 (up to 113 KB each: narrower tiles,
                                  two CTAs overlapping on each SM) */
   int32_t max_tile_cols;      /* cap on each job's tile width; 0 = the plan's */
-  int32_t reserved[2];
+  int32_t threads;            /* threads per CTA: 256 or 512 (0 = 512) */
+  int32_t reserved;
 } dr_batch_options;
 
 typedef struct {

@@ -127,7 +127,8 @@ def tuned_plan(geom, wires, edges, images, **kw):
     return plan, best
 
 
-BATCH_CANDIDATES = ((1, 0), (2, 0), (2, 64))   # (CTAs per SM, tile cap)
+# (CTAs per SM, tile-width cap, threads per CTA)
+BATCH_CANDIDATES = ((1, 0, 256), (1, 0, 512), (2, 0, 512), (2, 0, 256), (2, 64, 512))
 
 
 def tuned_batch(jobs, reps=2, stream=None):
@@ -139,9 +140,9 @@ def tuned_batch(jobs, reps=2, stream=None):
 
     stream = stream or torch.cuda.current_stream()
     best, timings = None, []
-    for per_sm, cap in BATCH_CANDIDATES:
+    for per_sm, cap, nt in BATCH_CANDIDATES:
         try:
-            b = dr.Batch(jobs, ctas_per_sm=per_sm, max_tile_cols=cap)
+            b = dr.Batch(jobs, ctas_per_sm=per_sm, max_tile_cols=cap, threads=nt)
         except dr.DrError:
             continue
         b.launch(stream)
@@ -153,13 +154,14 @@ def tuned_batch(jobs, reps=2, stream=None):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        timings.append({"ctas_per_sm": per_sm, "max_tile_cols": cap, "ms": ms})
+        timings.append({"ctas_per_sm": per_sm, "max_tile_cols": cap, "threads": nt, "ms": ms})
         if best is None or ms < best[0]:
             if best is not None:
                 best[1].close()
-            best = (ms, b, per_sm, cap)
+            best = (ms, b, per_sm, cap, nt)
         else:
             b.close()
     if best is None:
         raise RuntimeError("no batch configuration accepted")
-    return best[1], {"ctas_per_sm": best[2], "max_tile_cols": best[3], "candidates": timings}
+    return best[1], {"ctas_per_sm": best[2], "max_tile_cols": best[3], "threads": best[4],
+                     "candidates": timings}

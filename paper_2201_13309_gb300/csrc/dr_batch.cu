@@ -64,10 +64,12 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
   dr_batch_options opt;
   std::memset(&opt, 0, sizeof(opt));
   if (opt_in) opt = *opt_in;
-  if (opt.ctas_per_sm < 0 || opt.ctas_per_sm > 2 || opt.max_tile_cols < 0) {
-    set_error("dr_batch_create: ctas_per_sm must be 0, 1 or 2");
+  if (opt.ctas_per_sm < 0 || opt.ctas_per_sm > 2 || opt.max_tile_cols < 0 ||
+      (opt.threads != 0 && opt.threads != 256 && opt.threads != 512)) {
+    set_error("dr_batch_create: ctas_per_sm must be 0, 1 or 2 and threads 0, 256 or 512");
     return DR_ERR_INVALID_ARG;
   }
+  const int nthreads = opt.threads ? opt.threads : kBatchThreads;
   // shared memory each CTA may use so that ctas_per_sm CTAs share an SM
   const int want_per_sm = opt.ctas_per_sm == 0 ? 1 : opt.ctas_per_sm;
   const int smem_budget = std::min(kSmemPerCtaMax, kSmemPerSm / want_per_sm - 1024);
@@ -110,11 +112,11 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
       t.tile_cols /= 2;
     }
     const int lanes = t.tile_cols / 4;
-    if (smem > smem_budget || lanes > kBatchThreads) {
+    if (smem > smem_budget || lanes > nthreads) {
       set_error("dr_batch_create: job %d (%d steps) does not fit in shared memory", i, p->K);
       return DR_ERR_UNSUPPORTED;
     }
-    t.bin_groups = kBatchThreads / lanes;
+    t.bin_groups = nthreads / lanes;
     smem_max = std::max(smem_max, smem);
     BatchScan &d = desc[i];
     std::memset(&d, 0, sizeof(d));
@@ -150,6 +152,7 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
     return DR_ERR_OOM;
   }
   b->n = n;
+  b->threads = nthreads;
   b->n_items = items;
   b->out_dtype = out_dtype;
   b->smem = smem_max;
@@ -163,7 +166,7 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, smem_max);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nthreads, smem_max);
   if (e != cudaSuccess) {
     destroy(b);
     return cuda_fail("dr_batch_create: occupancy", e);
@@ -206,10 +209,10 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
     if (items > 0) {
       const int ns = (int)sorted.size();
       if (out_dtype == DR_OUT_BF16)
-        batch_rows_kernel<__nv_bfloat16><<<b->grid, kBatchThreads, smem_max, b->cap>>>(
+        batch_rows_kernel<__nv_bfloat16><<<b->grid, nthreads, smem_max, b->cap>>>(
             b->d_scans, ns, items, b->d_counter);
       else
-        batch_rows_kernel<float><<<b->grid, kBatchThreads, smem_max, b->cap>>>(
+        batch_rows_kernel<float><<<b->grid, nthreads, smem_max, b->cap>>>(
             b->d_scans, ns, items, b->d_counter);
     }
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &b->graph);
@@ -260,7 +263,7 @@ extern "C" dr_status dr_batch_get_info(const dr_batch_t *b, dr_batch_info *info)
   info->scans = b->n;
   info->items = b->n_items;
   info->grid = b->grid;
-  info->threads = kBatchThreads;
+  info->threads = b->threads;
   info->smem_bytes = b->smem;
   info->device_bytes = b->device_bytes;
   return DR_OK;

@@ -74,7 +74,7 @@ class Job(ctypes.Structure):
 
 class BatchOptions(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("max_tile_cols", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -312,7 +312,7 @@ class Batch:
     persistent launch replayed from a CUDA graph.  The tensors are bound at
     creation and must stay alive (and in place) while the batch exists."""
 
-    def __init__(self, jobs, ctas_per_sm=0, max_tile_cols=0):
+    def __init__(self, jobs, ctas_per_sm=0, max_tile_cols=0, threads=0):
         self._keep = list(jobs)
         self.ctas_per_sm = ctas_per_sm
         arr = (Job * len(jobs))()
@@ -324,6 +324,7 @@ class Batch:
         o = BatchOptions()
         o.ctas_per_sm = int(ctas_per_sm)
         o.max_tile_cols = int(max_tile_cols)
+        o.threads = int(threads)
         h = ctypes.c_void_p()
         check(lib().dr_batch_create(arr, len(jobs), ctypes.byref(o), ctypes.byref(h)))
         self._h = h

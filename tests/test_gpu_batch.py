@@ -60,15 +60,17 @@ def test_batch_matches_per_scan_launches_bitwise():
     assert np.all(np.abs(got - want) <= 1e-4 * s)
 
 
-@pytest.mark.parametrize("per_sm,cap", [(2, 0), (2, 64), (1, 32)])
-def test_batch_modes_agree(per_sm, cap):
+@pytest.mark.parametrize("per_sm,cap,nt", [(2, 0, 512), (2, 64, 512), (1, 32, 512), (1, 0, 256),
+                                           (2, 0, 256)])
+def test_batch_modes_agree(per_sm, cap, nt):
     jobs, refs = [], []
     for sc, edge in _scans():
         plan = dr.Plan(sc.geom, sc.wires, sc.edges, edge=edge)
         img = _dev(sc.images)
         refs.append(plan.reconstruct(img))
         jobs.append((plan, img, torch.full_like(refs[-1], float("nan"))))
-    batch = dr.Batch(jobs, ctas_per_sm=per_sm, max_tile_cols=cap)
+    batch = dr.Batch(jobs, ctas_per_sm=per_sm, max_tile_cols=cap, threads=nt)
+    assert batch.info()["threads"] == nt
     batch.launch()
     torch.cuda.synchronize()
     for (_, _, out), ref in zip(jobs, refs):
