@@ -149,6 +149,53 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def gpu_local_cpus(dev):
+    """CPUs local to the GPU (sysfs: the PCI device's local_cpulist, else its
+    NUMA node's cpulist), intersected with the CPUs this process may use."""
+    import torch
+
+    def parse(text):
+        cpus = set()
+        for part in text.strip().split(","):
+            if not part:
+                continue
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        return cpus
+
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        bus = f"{props.pci_domain_id:04x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+        base = f"/sys/bus/pci/devices/{bus}"
+        cpus = set()
+        if os.path.exists(f"{base}/local_cpulist"):
+            cpus = parse(open(f"{base}/local_cpulist").read())
+        if not cpus and os.path.exists(f"{base}/numa_node"):
+            node = int(open(f"{base}/numa_node").read())
+            if node >= 0:
+                cpus = parse(open(f"/sys/devices/system/node/node{node}/cpulist").read())
+        return sorted(cpus & os.sched_getaffinity(0))
+    except Exception:
+        return []
+
+
+class near_gpu:
+    """Run the enclosed host allocations on CPUs local to the GPU, so that
+    pinned pages are placed in the memory node next to it."""
+
+    def __init__(self, dev):
+        self.cpus = gpu_local_cpus(dev)
+
+    def __enter__(self):
+        self.saved = os.sched_getaffinity(0)
+        if self.cpus:
+            os.sched_setaffinity(0, self.cpus)
+        return self
+
+    def __exit__(self, *a):
+        os.sched_setaffinity(0, self.saved)
+
+
 def reduce_max(x, device):
     """Max of a float over all ranks (the slowest rank's time); identity on
     one process."""
@@ -452,13 +499,21 @@ def run_served(args, dev):
 
     from paper_2201_13309_gb300 import dr, synth
 
-    pool = []
+    pool, up_gbs = [], []
+    placement = near_gpu(dev)
     for s in range(args.pool):
         sp = synth.batch_scan_spec(s)
         img = synth.device_spot_images(sp.geom, sp.wires, sp.scat, seed=2000 + s,
                                        background=20.0, device=dev)
-        h = torch.empty(img.shape, dtype=torch.int16, pin_memory=True)
-        h.copy_(img)
+        with placement:
+            h = torch.empty(img.shape, dtype=torch.int16, pin_memory=True)
+            h.copy_(img)
+        # one timed upload of this pinned buffer (placement check)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        img.copy_(h, non_blocking=True)
+        torch.cuda.synchronize()
+        up_gbs.append(h.numel() * 2 / (time.perf_counter() - t0) / 1e9)
         pool.append((sp, h))
         del img
     torch.cuda.empty_cache()
@@ -476,7 +531,7 @@ def run_served(args, dev):
     for rate in rates:
         rng = np.random.Generator(np.random.PCG64(1000 + int(rate)))
         gaps = rng.exponential(1.0 / rate, args.served_scans)
-        ids, lat = [], []
+        ids, lat, parts = [], [], []
         lock = th.Lock()
         have = th.Semaphore(0)
 
@@ -488,6 +543,9 @@ def run_served(args, dev):
                 srv.wait(rid)
                 _, t = srv.fetch(rid)
                 lat.append(t["done"] - t["submitted"])
+                parts.append((i % len(pool), t["admitted"] - t["submitted"],
+                              t["planned"] - t["admitted"], t["uploaded"] - t["planned"],
+                              t["done"] - t["uploaded"]))
                 srv.release(rid)
 
         ct = th.Thread(target=consumer)
@@ -507,11 +565,23 @@ def run_served(args, dev):
         ct.join()
         wall = time.perf_counter() - t0
         lat_ms = np.array(lat) * 1e3
+        pa = np.array([p[1:] for p in parts]) * 1e3
+        per_scan = {}
+        for (idx, q, pl, u, k), l in zip(parts, lat_ms):
+            per_scan.setdefault(idx, []).append(l)
         results.append({"offered_scans_per_s": rate, "scans": args.served_scans,
                         "achieved_scans_per_s": args.served_scans / wall,
                         "p50_ms": float(np.percentile(lat_ms, 50)),
                         "p99_ms": float(np.percentile(lat_ms, 99)),
-                        "mean_ms": float(lat_ms.mean()), "max_ms": float(lat_ms.max())})
+                        "mean_ms": float(lat_ms.mean()), "max_ms": float(lat_ms.max()),
+                        "phase_p50_ms": {n: float(np.percentile(pa[:, c], 50)) for c, n in
+                                         enumerate(("queue", "plan", "upload", "kernel"))},
+                        "phase_p99_ms": {n: float(np.percentile(pa[:, c], 99)) for c, n in
+                                         enumerate(("queue", "plan", "upload", "kernel"))},
+                        "per_pool_scan_median_ms": {
+                            f"{pool[i][0].geom['rows']}x{pool[i][0].geom['cols']}"
+                            f"_K{pool[i][0].K}_B{pool[i][0].B}": float(np.median(v))
+                            for i, v in sorted(per_scan.items())}})
         print(json.dumps({"served_rate": results[-1]}), file=sys.stderr, flush=True)
     st = srv.stats()
     srv.close()
@@ -550,6 +620,9 @@ def run_served(args, dev):
     mean_in = float(np.mean([h.numel() * 2 for _, h in pool])) / 1e9
     return {"mode": "served", "metric": "scans/s and p50/p99 latency (arrival -> result on device)",
             "budget_GB": args.budget_gb, "slots": args.slots, "pool_scans": len(pool),
+            "pinned_upload_GBps": {"min": float(min(up_gbs)), "median": float(np.median(up_gbs)),
+                                   "max": float(max(up_gbs))},
+            "alloc_cpus": placement.cpus,
             "mean_input_GB": mean_in, "rates": results,
             "plan_cache": {"plans_built": st["plans_built"], "failed": st["failed"],
                            "cold_first_request_ms": {"p50": float(np.percentile(cold, 50)),
@@ -706,9 +779,11 @@ def main():
     # the unpipelined form (whole upload, kernel, whole download) beside it
     e2e = None
     if not args.no_e2e:
-        h_img = torch.empty(images.shape, dtype=torch.int16, pin_memory=True)
-        h_img.copy_(images)
-        h_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+        with near_gpu(dev):
+            h_img = torch.empty(images.shape, dtype=torch.int16, pin_memory=True)
+            h_img.copy_(images)
+            h_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+            h_out.zero_()
         slab = args.slab_rows
         per = (-(-slab * spec.geom["cols"] * spec.K * 2 // 256) * 256
                + -(-slab * spec.geom["cols"] * spec.B * 4 // 256) * 256)

@@ -254,9 +254,11 @@ typedef struct {
 enum { DR_REQ_QUEUED = 0, DR_REQ_UPLOADING = 1, DR_REQ_RUNNING = 2, DR_REQ_DONE = 3,
        DR_REQ_FAILED = 4 };
 
-/* Seconds since the server was created (host steady clock). */
+/* Seconds since the server was created (host steady clock): queued, admitted
+ * (slot and memory reserved), planned (plan found or built), uploaded (the
+ * upload, which waits behind earlier uploads, is done), done (kernel done). */
 typedef struct {
-  double submitted, admitted, uploaded, done;
+  double submitted, admitted, planned, uploaded, done;
 } dr_request_times;
 
 typedef struct {

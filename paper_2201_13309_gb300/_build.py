@@ -1,8 +1,11 @@
 """Compile libdr.so (the CUDA library behind include/dr.h) for sm_103a.
 
 Each translation unit is compiled in parallel with nvcc, then linked into an
-in-tree shared library next to this file.  The CUDA runtime is linked
-statically so the library has no dependency beyond the driver.
+in-tree shared library next to this file.  The CUDA runtime is linked as the
+shared libcudart.so, so that the library and its host program (PyTorch, or a
+C program) use one runtime: a second, static runtime does not know the host
+program's pinned buffers and copies from them at a fraction of the link's
+bandwidth the first time it sees each one.
 """
 from __future__ import annotations
 
@@ -67,7 +70,9 @@ def build(force=False, verbose=False, ptxas_info=False):
         if failed:
             raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
         tmp_lib = LIB + f".tmp{os.getpid()}"
-        subprocess.run([cc, *ARCH, "-shared", "-o", tmp_lib, *objs], check=True)
+        cudalib = os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")
+        subprocess.run([cc, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", "-rpath",
+                        "-Xlinker", cudalib, "-o", tmp_lib, *objs], check=True)
         os.replace(tmp_lib, LIB)
     finally:
         shutil.rmtree(tmp, ignore_errors=True)

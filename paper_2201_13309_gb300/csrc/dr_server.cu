@@ -117,7 +117,9 @@ struct dr_server {
   dr_server_options opt{};
   unsigned char *base = nullptr;
   Arena arena;
-  std::vector<cudaStream_t> streams;
+  std::vector<cudaStream_t> streams;   // one compute stream per slot
+  std::vector<cudaEvent_t> up_done;    // per slot: its request's upload is done
+  cudaStream_t up = nullptr;           // uploads, one at a time in admission order
   std::vector<int> slot_busy;
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
@@ -162,7 +164,7 @@ void CUDART_CB on_uploaded(void *arg) {
   Request *r = static_cast<Request *>(arg);
   std::lock_guard<std::mutex> lk(r->srv->mu);
   r->t.uploaded = now_s() - r->srv->t0;
-  r->state = DR_REQ_RUNNING;
+  if (r->state == DR_REQ_UPLOADING) r->state = DR_REQ_RUNNING;
 }
 
 void CUDART_CB on_done(void *arg) {
@@ -295,20 +297,33 @@ void scheduler(dr_server_t *s) {
           evict_plans(s, &dead);
         }
       }
+      {
+        std::lock_guard<std::mutex> g(s->mu);
+        r->t.planned = now_s() - s->t0;
+      }
       cudaStream_t cs = s->streams[r->slot];
       uint16_t *d_img = reinterpret_cast<uint16_t *>(s->base + r->img_off);
       void *d_out = s->base + r->out_off;
       if (st == DR_OK) {
+        // uploads share the host link: one at a time, in admission order, so
+        // each finishes as early as possible; the slot's kernel waits for it
         cudaError_t e = cudaMemcpyAsync(d_img, r->h_images, r->img_bytes,
-                                        cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess) e = cudaLaunchHostFunc(cs, on_uploaded, r);
+                                        cudaMemcpyHostToDevice, s->up);
+        // the event follows the callback, so on_uploaded always runs before
+        // the kernel (and its on_done) can start
+        if (e == cudaSuccess) e = cudaLaunchHostFunc(s->up, on_uploaded, r);
+        if (e == cudaSuccess) e = cudaEventRecord(s->up_done[r->slot], s->up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, s->up_done[r->slot], 0);
         st = e == cudaSuccess ? dr_reconstruct(r->pe->plan, d_img, d_out, (dr_stream_t)cs)
                               : cuda_fail("server upload", e);
         if (st == DR_OK) {
           e = cudaLaunchHostFunc(cs, on_done, r);
           if (e != cudaSuccess) st = cuda_fail("server completion callback", e);
         }
-        if (st != DR_OK) cudaStreamSynchronize(cs);  // let the slot drain before reuse
+        if (st != DR_OK) {  // let the slot (and its upload) drain before reuse
+          cudaStreamSynchronize(s->up);
+          cudaStreamSynchronize(cs);
+        }
       }
       if (st != DR_OK) failed.emplace_back(r, st);
     }
@@ -361,15 +376,17 @@ extern "C" dr_status dr_server_create(const dr_server_options *o, dr_server_t **
     return cuda_fail("dr_server_create", e);
   }
   s->arena.reset(o->budget_bytes);
-  s->streams.resize(s->opt.slots);
+  s->streams.assign(s->opt.slots, nullptr);
+  s->up_done.assign(s->opt.slots, nullptr);
   s->slot_busy.assign(s->opt.slots, 0);
-  for (auto &st : s->streams) {
-    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-      st = nullptr;
-      dr_server_destroy(s);
-      return cuda_fail("dr_server_create: stream", e);
-    }
+  e = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking);
+  for (int i = 0; i < s->opt.slots && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->up_done[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    dr_server_destroy(s);
+    return cuda_fail("dr_server_create: streams", e);
   }
   // load the kernels now, while no stream has work: loading a module later
   // can synchronize the context
@@ -567,11 +584,17 @@ extern "C" void dr_server_destroy(dr_server_t *s) {
   }
   s->cv_sched.notify_all();
   if (s->sched.joinable()) s->sched.join();
+  if (s->up) {
+    cudaStreamSynchronize(s->up);
+    cudaStreamDestroy(s->up);
+  }
   for (auto st : s->streams)
     if (st) {
       cudaStreamSynchronize(st);
       cudaStreamDestroy(st);
     }
+  for (auto ev : s->up_done)
+    if (ev) cudaEventDestroy(ev);
   for (auto &kv : s->reqs) delete kv.second;
   for (auto &kv : s->plans) dr_plan_destroy(kv.second.plan);
   if (s->base) cudaFree(s->base);
