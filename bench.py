@@ -635,6 +635,50 @@ def run_served(args, dev):
                          "+-400 um) held in pinned host memory")}
 
 
+def run_pixels(args, spec, images, dev):
+    """The paper's pixel-percentage sweep on the full-detector scan: the
+    pixels carrying the most signal (activity = sum |dI|) are selected and
+    only they are reconstructed (compacted output), against the full scan."""
+    import torch
+
+    from paper_2201_13309_gb300 import dr
+
+    plan = dr.Plan(spec.geom, spec.wires, spec.edges)
+    out_full = plan.empty_output(dev)
+
+    def t(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    full_ms = t(lambda: plan.reconstruct(images, out_full))
+    act = dr.pixel_activity(images)
+    act_ms = t(lambda: dr.pixel_activity(images))
+    flat = act.reshape(-1)
+    vals = flat.cpu().numpy()
+    rows = []
+    for pct in (25, 50, 100):
+        thr = float(np.percentile(vals, 100 - pct)) if pct < 100 else -1.0
+        sel_ms = t(lambda: dr.select_pixels(flat, thr))
+        idx, n = dr.select_pixels(flat, thr)
+        out = torch.empty((spec.B, n), dtype=torch.float32, device=dev)
+        rec_ms = t(lambda: plan.reconstruct_selected(images, idx, n, out), reps=3)
+        ok = bool(torch.equal(out[:, ::max(1, n // 4096)].view(torch.int32),
+                              out_full.reshape(spec.B, -1)[:, idx.long()][:, ::max(1, n // 4096)]
+                              .view(torch.int32)))
+        rows.append({"percent": pct, "pixels": n, "activity_ms": act_ms, "select_ms": sel_ms,
+                     "reconstruct_ms": rec_ms, "total_ms": act_ms + sel_ms + rec_ms,
+                     "equal_to_full": ok})
+        del out
+    return {"mode": "pixels", "workload": WORKLOAD, "full_scan_ms": full_ms, "sweep": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -647,7 +691,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--mode", default="plain",
-                    choices=["plain", "precision", "batched", "served"])
+                    choices=["plain", "precision", "batched", "served", "pixels"])
     ap.add_argument("--rates", default="5,20,50")
     ap.add_argument("--served-scans", type=int, default=1000)
     ap.add_argument("--saturation-scans", type=int, default=96)
@@ -715,6 +759,10 @@ def main():
     if args.mode == "precision":
         if rank == 0:
             print(json.dumps(run_precision(args, spec, images, dev)), flush=True)
+        return 0
+    if args.mode == "pixels":
+        if rank == 0:
+            print(json.dumps(run_pixels(args, spec, images, dev)), flush=True)
         return 0
 
     from paper_2201_13309_gb300 import autotune

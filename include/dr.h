@@ -162,6 +162,29 @@ dr_status dr_reconstruct_streamed(const dr_plan_t *plan, const uint16_t *h_image
                                   void *h_out, void *d_workspace, size_t workspace_bytes,
                                   int32_t slab_rows, dr_stream_t stream);
 
+/* ---- Pixel selection (the paper's pixel-percentage experiment, Sec. IV-A) --
+ * Only some pixels carry signal (diffraction spots); these calls reconstruct
+ * only the selected ones into a compacted output.
+ * dr_pixel_activity: d_activity[p] = sum_k |I_k(p) - I_{k+1}(p)| (exact,
+ *   stored as float; K <= 32768) for the [K][rows][cols] stack, p row-major.
+ * dr_select_pixels: the indices p (0..n-1) with d_activity[p] >= threshold,
+ *   in increasing order, into d_index (room for n entries); the number of them
+ *   into the device int32 *d_count.  Needs dr_select_scratch_bytes(n) bytes of
+ *   device scratch (caller-owned).
+ * dr_reconstruct_selected: bins of the listed pixels only, compacted:
+ *   d_out[j * n + i] is bin j of pixel d_index[i] (FP32 or BF16 per the plan),
+ *   bitwise equal to dr_reconstruct's value for that pixel.  n is the host
+ *   count of listed pixels. */
+dr_status dr_pixel_activity(const uint16_t *d_images, int32_t K, int32_t rows, int32_t cols,
+                            float *d_activity, dr_stream_t stream);
+size_t dr_select_scratch_bytes(int64_t n);
+dr_status dr_select_pixels(const float *d_activity, int64_t n, float threshold,
+                           int32_t *d_index, int32_t *d_count, void *d_scratch,
+                           size_t scratch_bytes, dr_stream_t stream);
+dr_status dr_reconstruct_selected(const dr_plan_t *plan, const uint16_t *d_images,
+                                  const int32_t *d_index, int32_t n, void *d_out,
+                                  dr_stream_t stream);
+
 /* The exact integer differences the kernels use (Sec. III-C "difference
  * intensity at each pixel"): d_diff[k][p] = images[k][p] - images[k+1][p] as
  * int32, k = 0..K-2, for a [K][rows][cols] uint16 device stack. */

@@ -588,3 +588,94 @@ __global__ void depths_kernel(const Consts c, int kernel, int r0, int nrows, dou
 }
 
 }  // namespace dr
+
+namespace dr {
+
+// ---------------------------------------------------- pixel selection ---
+// The paper's second experiment varies the percentage of pixels processed
+// (Sec. IV-A).  Here a pixel's activity is its total intensity change
+// sum_k |I_k - I_{k+1}| (exact); pixels at or above a threshold are
+// compacted, in order, into an index list, and only those are reconstructed
+// into a compacted [B][n] output.
+
+constexpr int kSelChunk = 4096;  // pixels per block in the compaction kernels
+
+// Reconstruction of listed pixels (compacted output out[j * n + i]).  With
+// the plan's per-row tables (row-shared geometry) each lane reads its row's
+// (k, f) entries and only the bins in the row's data range touch the images;
+// otherwise it runs the per-pixel merge-walk of pixels_kernel on images read
+// from global memory.  Both give the full reconstruction's values bitwise.
+template <class Geo, class OutT>
+__global__ void __launch_bounds__(256) selected_kernel(const Consts c, int kernel,
+                                                       const uint16_t *__restrict__ img,
+                                                       const int32_t *__restrict__ idx, int n,
+                                                       OutT *__restrict__ out) {
+  using pos_t = typename Geo::pos_t;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p = idx[i], K = c.K, B = c.B;
+  const size_t plane = (size_t)c.H * c.W;
+  const int row = p / c.W;
+  const bool rev = c.reverse != 0;
+  auto px = [&](int k) { return biased(__ldg(img + (size_t)(rev ? K - 1 - k : k) * plane + p)); };
+  const float sign = c.out_sign;
+  const float I0 = px(0);
+  OutT *o = out + i;
+  if (kernel == DR_KERNEL_ROWS && c.tab != nullptr) {
+    const int2 *trow = c.tab + (size_t)row * c.tab_stride;
+    const int2 nz = __ldg(trow);
+    const int2 *tab = trow + 1;
+    const float zero = __fmul_rn(sign, 0.f);
+    for (int j = 0; j < nz.x; ++j, o += n) st_cs(o, zero);
+    int kcur = -2;  // nothing loaded yet: the first entry always loads both
+    float Ik = 0.f, Ik1 = 0.f;
+    auto evalF = [&](int2 kf) {
+      if (kf.x != kcur) {
+        if (kcur >= 0 && kf.x == kcur + 1) {
+          Ik = Ik1;
+        } else {
+          Ik = px(kf.x);
+        }
+        Ik1 = px(kf.x + 1);
+        kcur = kf.x;
+      }
+      return __fmaf_rn(__int_as_float(kf.y), __fsub_rn(Ik, Ik1), __fsub_rn(I0, Ik));
+    };
+    if (nz.x < nz.y) {
+      float Fp = evalF(__ldg(tab + nz.x));
+      for (int j = nz.x; j < nz.y; ++j, o += n) {
+        const float F = evalF(__ldg(tab + j + 1));
+        st_cs(o, __fmul_rn(sign, __fsub_rn(F, Fp)));
+        Fp = F;
+      }
+    }
+    for (int j = max(nz.y, nz.x); j < B; ++j, o += n) st_cs(o, zero);
+    return;
+  }
+  const auto g = Geo::group(c, kernel == DR_KERNEL_ROWS ? row : p);
+  const auto *steps = Geo::steps(c);
+  int k = 0;
+  pos_t t0 = Geo::depth(g, steps[0], c), t1 = Geo::depth(g, steps[1], c);
+  auto inv = Geo::inv_len(t0, t1);
+  float Ik = I0, Ik1 = px(1), Fp = 0.f;
+  for (int j = 0; j <= B; ++j) {
+    const pos_t e = Geo::edge(c, j);
+    while (k < K - 2 && t1 < e) {
+      ++k;
+      t0 = t1;
+      t1 = Geo::depth(g, steps[k + 1], c);
+      inv = Geo::inv_len(t0, t1);
+      Ik = Ik1;
+      Ik1 = px(k + 1);
+    }
+    const float f = Geo::frac(e, t0, inv);
+    const float F = __fmaf_rn(f, __fsub_rn(Ik, Ik1), __fsub_rn(I0, Ik));
+    if (j > 0) {
+      st_cs(o, __fmul_rn(sign, __fsub_rn(F, Fp)));
+      o += n;
+    }
+    Fp = F;
+  }
+}
+
+}  // namespace dr

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -531,5 +532,235 @@ extern "C" dr_status dr_reconstruct_streamed(const dr_plan_t *p, const uint16_t 
   e = cudaEventRecord(ss->down_done[0], ss->down);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ss->down_done[0], 0);
   if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: join", e);
+  return DR_OK;
+}
+
+// ------------------------------------------------------ pixel selection ---
+
+namespace dr {
+// Two adjacent pixels per thread (one 32-bit load per step when P is even),
+// steps unrolled so that several loads are in flight per thread.
+__global__ void activity_kernel(const uint16_t *__restrict__ img, int K, long long P,
+                                float *__restrict__ act) {
+  const long long pairs = (P + 1) / 2;
+  const bool even = (P % 2) == 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < pairs;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long p = 2 * q;
+    const bool two = p + 1 < P;
+    auto ld = [&](int k, int &a, int &b) {
+      const size_t o = (size_t)k * P + p;
+      if (even) {
+        const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(img + o));
+        a = (int)(w & 0xFFFFu);
+        b = (int)(w >> 16);
+      } else {
+        a = __ldg(img + o);
+        b = two ? __ldg(img + o + 1) : 0;
+      }
+    };
+    int pa, pb, sa = 0, sb = 0;
+    ld(0, pa, pb);
+    int k = 1;
+    for (; k + 3 < K; k += 4) {
+      int a0, b0, a1, b1, a2, b2, a3, b3;
+      ld(k, a0, b0);
+      ld(k + 1, a1, b1);
+      ld(k + 2, a2, b2);
+      ld(k + 3, a3, b3);
+      sa += abs(pa - a0) + abs(a0 - a1) + abs(a1 - a2) + abs(a2 - a3);
+      sb += abs(pb - b0) + abs(b0 - b1) + abs(b1 - b2) + abs(b2 - b3);
+      pa = a3;
+      pb = b3;
+    }
+    for (; k < K; ++k) {
+      int a, b;
+      ld(k, a, b);
+      sa += abs(pa - a);
+      sb += abs(pb - b);
+      pa = a;
+      pb = b;
+    }
+    act[p] = (float)sa;
+    if (two) act[p + 1] = (float)sb;
+  }
+}
+
+// pass 1: selected pixels per chunk
+__global__ void select_count_kernel(const float *__restrict__ act, long long n, float thr,
+                                    int *__restrict__ counts) {
+  __shared__ int total;
+  if (threadIdx.x == 0) total = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * kSelChunk;
+  int mine = 0;
+  for (int i = threadIdx.x; i < kSelChunk; i += blockDim.x) {
+    const long long p = base + i;
+    mine += (p < n && act[p] >= thr);
+  }
+  atomicAdd(&total, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) counts[blockIdx.x] = total;
+}
+
+// pass 2 (one block): exclusive scan of the chunk counts, total to *count
+__global__ void select_scan_kernel(int *__restrict__ counts, int nchunks, int *__restrict__ count) {
+  __shared__ int carry;
+  __shared__ int warp_sums[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nchunks; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < nchunks ? counts[i] : 0;
+    int x = v;  // inclusive warp scan
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int ws = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += y;
+      }
+      warp_sums[lane] = ws;  // inclusive over warps
+    }
+    __syncthreads();
+    const int before = carry + (w > 0 ? warp_sums[w - 1] : 0) + x - v;
+    if (i < nchunks) counts[i] = before;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = carry;
+}
+
+// pass 3: each chunk writes its selected indices, in order, at its offset
+__global__ void select_write_kernel(const float *__restrict__ act, long long n, float thr,
+                                    const int *__restrict__ offsets, int32_t *__restrict__ idx) {
+  __shared__ int warp_base[32];
+  __shared__ int running;
+  if (threadIdx.x == 0) running = offsets[blockIdx.x];
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * kSelChunk;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i0 = 0; i0 < kSelChunk; i0 += blockDim.x) {
+    const long long p = base + i0 + threadIdx.x;
+    const bool sel = p < n && act[p] >= thr;
+    const unsigned m = __ballot_sync(0xffffffffu, sel);
+    if (lane == 0) warp_base[w] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {  // warp offsets in order
+      int acc = running;
+      for (int q = 0; q < nw; ++q) {
+        const int c = warp_base[q];
+        warp_base[q] = acc;
+        acc += c;
+      }
+      running = acc;
+    }
+    __syncthreads();
+    if (sel) idx[warp_base[w] + __popc(m & ((1u << lane) - 1u))] = (int32_t)p;
+    __syncthreads();
+  }
+}
+
+}  // namespace dr
+
+extern "C" dr_status dr_pixel_activity(const uint16_t *img, int32_t K, int32_t rows, int32_t cols,
+                                       float *act, dr_stream_t stream) {
+  const long long P = (long long)rows * cols;
+  if (K < 1 || rows < 0 || cols < 0) {
+    set_error("dr_pixel_activity: bad sizes");
+    return DR_ERR_INVALID_ARG;
+  }
+  if (P == 0) return DR_OK;
+  if (!img || !act) {
+    set_error("dr_pixel_activity: null buffer");
+    return DR_ERR_INVALID_ARG;
+  }
+  if ((long long)K * 65535 > 2147483647LL) {
+    set_error("dr_pixel_activity: K too large for an exact int32 sum");
+    return DR_ERR_UNSUPPORTED;
+  }
+  if (P % 2 == 0 && ((uintptr_t)img & 3) != 0) {
+    set_error("dr_pixel_activity: images not 4-byte aligned");
+    return DR_ERR_INVALID_ARG;
+  }
+  const int blocks = (int)std::min<long long>(((P + 1) / 2 + 255) / 256, 152 * 16);
+  activity_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(img, K, P, act);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("dr_pixel_activity", e);
+  return DR_OK;
+}
+
+extern "C" size_t dr_select_scratch_bytes(int64_t n) {
+  const long long chunks = (n + kSelChunk - 1) / kSelChunk;
+  return (size_t)std::max<long long>(chunks, 1) * sizeof(int);
+}
+
+extern "C" dr_status dr_select_pixels(const float *act, int64_t n, float threshold,
+                                      int32_t *idx, int32_t *count, void *scratch,
+                                      size_t scratch_bytes, dr_stream_t stream) {
+  if (n < 0 || n > 2147483647LL || !act || !idx || !count || !scratch) {
+    set_error("dr_select_pixels: bad arguments");
+    return DR_ERR_INVALID_ARG;
+  }
+  if (scratch_bytes < dr_select_scratch_bytes(n)) {
+    set_error("dr_select_pixels: scratch of %zu bytes, need %zu", scratch_bytes,
+              dr_select_scratch_bytes(n));
+    return DR_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int chunks = (int)((n + kSelChunk - 1) / kSelChunk);
+  int *counts = static_cast<int *>(scratch);
+  if (chunks == 0) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_fail("dr_select_pixels", e);
+    return DR_OK;
+  }
+  select_count_kernel<<<chunks, 256, 0, st>>>(act, n, threshold, counts);
+  select_scan_kernel<<<1, 1024, 0, st>>>(counts, chunks, count);
+  select_write_kernel<<<chunks, 256, 0, st>>>(act, n, threshold, counts, idx);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("dr_select_pixels", e);
+  return DR_OK;
+}
+
+extern "C" dr_status dr_reconstruct_selected(const dr_plan_t *p, const uint16_t *img,
+                                             const int32_t *idx, int32_t n, void *out,
+                                             dr_stream_t stream) {
+  if (!p || n < 0) {
+    set_error("dr_reconstruct_selected: bad arguments");
+    return DR_ERR_INVALID_ARG;
+  }
+  if (n == 0 || (size_t)p->rows * p->cols == 0) return DR_OK;
+  if (!img || !idx || !out) {
+    set_error("dr_reconstruct_selected: null buffer");
+    return DR_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = (n + 255) / 256;
+  const bool bf16 = p->out_dtype == DR_OUT_BF16;
+  if (p->geom_prec == DR_GEOM_FP64) {
+    if (bf16)
+      selected_kernel<GeoF64, __nv_bfloat16><<<blocks, 256, 0, st>>>(
+          p->c, p->kernel, img, idx, n, (__nv_bfloat16 *)out);
+    else
+      selected_kernel<GeoF64, float><<<blocks, 256, 0, st>>>(p->c, p->kernel, img, idx, n,
+                                                             (float *)out);
+  } else {
+    if (bf16)
+      selected_kernel<GeoFx, __nv_bfloat16><<<blocks, 256, 0, st>>>(
+          p->c, p->kernel, img, idx, n, (__nv_bfloat16 *)out);
+    else
+      selected_kernel<GeoFx, float><<<blocks, 256, 0, st>>>(p->c, p->kernel, img, idx, n,
+                                                            (float *)out);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("dr_reconstruct_selected", e);
   return DR_OK;
 }

@@ -33,7 +33,8 @@ EXPORTS = ("dr_plan", "dr_plan_destroy", "dr_plan_get_info", "dr_plan_device_byt
            "dr_batch_check", "dr_batch_get_info", "dr_batch_destroy", "dr_server_create",
            "dr_server_submit", "dr_server_poll", "dr_server_wait", "dr_server_fetch",
            "dr_server_fetch_into", "dr_server_release", "dr_server_get_stats",
-           "dr_server_destroy", "dr_reconstruct_streamed")
+           "dr_server_destroy", "dr_reconstruct_streamed", "dr_pixel_activity",
+           "dr_select_scratch_bytes", "dr_select_pixels", "dr_reconstruct_selected")
 REQ_STATES = {0: "queued", 1: "uploading", 2: "running", 3: "done", 4: "failed"}
 
 _d3 = ctypes.c_double * 3
@@ -153,6 +154,10 @@ def lib():
                 "dr_server_get_stats": ([P, ctypes.POINTER(ServerStats)], I32),
                 "dr_server_destroy": ([P], None),
                 "dr_reconstruct_streamed": ([P, P, P, P, SZ, I32, P], I32),
+                "dr_pixel_activity": ([P, I32, I32, I32, P, P], I32),
+                "dr_select_scratch_bytes": ([ctypes.c_int64], SZ),
+                "dr_select_pixels": ([P, ctypes.c_int64, ctypes.c_float, P, P, P, SZ, P], I32),
+                "dr_reconstruct_selected": ([P, P, P, I32, P, P], I32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -273,6 +278,19 @@ class Plan:
             workspace.numel() * workspace.element_size(), int(slab_rows),
             ctypes.c_void_p(_stream_handle(stream))))
         return h_out
+
+    def reconstruct_selected(self, images, index, n=None, out=None, stream=None):
+        """Bins of the listed pixels only: out [B, n], out[:, i] = bin values
+        of pixel index[i] (row-major).  n defaults to len(index)."""
+        import torch
+        n = int(index.numel() if n is None else n)
+        if out is None:
+            out = torch.empty((self.B, n), dtype=self.out_torch_dtype(), device=images.device)
+        if tuple(images.shape) != (self.K, self.rows, self.cols) or out.shape[1] < n:
+            raise ValueError("shape mismatch")
+        check(lib().dr_reconstruct_selected(self._h, _dptr(images), _dptr(index), n,
+                                            _dptr(out), ctypes.c_void_p(_stream_handle(stream))))
+        return out
 
     def depths(self, r0=0, nrows=None, stream=None):
         """The GPU's depths d_k (mm) for rows r0..: CUDA float64 [nrows, cols, K]."""
@@ -449,6 +467,32 @@ def reconstruct_rows_static(geom, wires, edges, images, out, status=None, edge="
         None if images is None else _dptr(images), None if out is None else _dptr(out),
         None if status is None else _dptr(status), ctypes.c_void_p(_stream_handle(stream))))
     return out
+
+
+def pixel_activity(images, stream=None):
+    """float32 [rows, cols]: sum_k |I_k - I_{k+1}| per pixel (exact)."""
+    import torch
+    K, H, W = images.shape
+    act = torch.empty((H, W), dtype=torch.float32, device=images.device)
+    check(lib().dr_pixel_activity(_dptr(images), K, H, W, _dptr(act),
+                                  ctypes.c_void_p(_stream_handle(stream))))
+    return act
+
+
+def select_pixels(activity, threshold, stream=None):
+    """(int32 index tensor of the pixels with activity >= threshold, in
+    increasing row-major order; their count)."""
+    import torch
+    n = activity.numel()
+    idx = torch.empty(max(n, 1), dtype=torch.int32, device=activity.device)
+    cnt = torch.zeros(1, dtype=torch.int32, device=activity.device)
+    scratch = torch.empty(int(lib().dr_select_scratch_bytes(n)), dtype=torch.uint8,
+                          device=activity.device)
+    check(lib().dr_select_pixels(_dptr(activity), n, float(threshold), _dptr(idx), _dptr(cnt),
+                                 _dptr(scratch), scratch.numel(),
+                                 ctypes.c_void_p(_stream_handle(stream))))
+    count = int(cnt.item())
+    return idx[:count], count
 
 
 def version():

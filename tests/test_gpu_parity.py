@@ -285,3 +285,23 @@ def test_full_detector_sampled_rows():
         sel = err[inside[r0:r0 + 256]]
         if sel.numel():
             assert float(sel.max()) <= 0.0
+
+
+@pytest.mark.slow
+def test_maximum_size_sampled_rows():
+    """The largest scan shape the uneven batch draws: 2048x2048 pixels, 801
+    steps, 1601 bins of 0.5 um (6.7 GB in, 26.9 GB out)."""
+    spec = synth.full_scan_spec(3)
+    spec.wires = synth.wire_path(801)
+    spec.edges = synth.bin_edges(-400.0, 400.0, 0.5)
+    img = synth.device_spot_images(spec.geom, spec.wires, spec.scat, 3, 20.0, "cuda")
+    plan = dr.Plan(spec.geom, spec.wires, spec.edges)
+    out = plan.reconstruct(img)
+    torch.cuda.synchronize()
+    plan.check_device()
+    for r in (0, 700, 1500, 2047):
+        host = img[:, r:r + 1, :].cpu().numpy().view(np.uint16)
+        ref = O.reconstruct(row_geometry(spec.geom, r), spec.wires, host, spec.edges)
+        assert_parity(out[:, r:r + 1, :].cpu().numpy(), ref, host)
+    del out, img
+    torch.cuda.empty_cache()
