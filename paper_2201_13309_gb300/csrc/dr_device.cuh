@@ -678,4 +678,99 @@ __global__ void __launch_bounds__(256) selected_kernel(const Consts c, int kerne
   }
 }
 
+
+// First position i in the sorted list idx[0..n) with idx[i] >= target, found
+// by one warp (32 probes per round); every lane returns it.
+__device__ __forceinline__ int warp_lower_bound(const int32_t *idx, int n, int target) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = n;  // answer in [lo, hi]
+  while (hi - lo > 31) {  // the final round covers hi - lo + 1 <= 32 positions
+    const int m = hi - lo;
+    const int pos = lo + (int)(((long long)m * lane) / 32);
+    const bool ge = __ldg(idx + pos) >= target;
+    const unsigned b = __ballot_sync(0xffffffffu, ge);
+    if (b == 0) {
+      lo = lo + (int)(((long long)m * 31) / 32) + 1;
+    } else {
+      const int f = __ffs(b) - 1;  // first probe >= target
+      const int nhi = lo + (int)(((long long)m * f) / 32);
+      const int nlo = f == 0 ? lo : lo + (int)(((long long)m * (f - 1)) / 32) + 1;
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  const int pos = lo + lane;
+  const bool ge = pos >= hi || __ldg(idx + pos) >= target;
+  const unsigned b = __ballot_sync(0xffffffffu, ge);
+  return lo + __ffs(b) - 1;
+}
+
+// Listed pixels of row-shared geometry, staged like rows_tile: one CTA per
+// (row, column tile); tiles without listed pixels load nothing; each thread
+// streams the bins of one listed pixel from shared memory into the compacted
+// output out[j * n + i].  Needs the plan's row tables; TMA only.
+template <class OutT>
+__global__ void __launch_bounds__(256) selected_rows_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                            const Consts c, const Tuning t,
+                                                            const int32_t *__restrict__ idx, int n,
+                                                            OutT *__restrict__ out) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  int *range = reinterpret_cast<int *>(smem + 16);
+  uint16_t *simg = reinterpret_cast<uint16_t *>(smem + 128);
+  const int TC = t.tile_cols, K = c.K, B = c.B;
+  const int Kpad = t.kc * t.nchunks;
+  int2 *stab0 = reinterpret_cast<int2 *>(smem + 128 + align16((size_t)Kpad * TC * 2) +
+                                         align16((size_t)K * sizeof(int32_t)));
+  const int row = blockIdx.y, c0 = blockIdx.x * TC;
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    const int first = row * c.W + c0;
+    const int lo = warp_lower_bound(idx, n, first);
+    const int hi = warp_lower_bound(idx, n, first + min(TC, c.W - c0));
+    if (tid == 0) {
+      range[0] = lo;
+      range[1] = hi;
+      mbar_init(bar, 1);
+    }
+  }
+  __syncthreads();
+  const int lo = range[0], hi = range[1];
+  if (lo >= hi) return;  // nothing listed in this tile
+  const int2 *grow = c.tab + (size_t)row * c.tab_stride;
+  if (tid == 0) {
+    const uint32_t tab_bytes = (uint32_t)c.tab_stride * 8u;
+    mbar_expect_tx(bar, (uint32_t)(Kpad * TC * 2) + tab_bytes);
+    for (int ch = 0; ch < t.nchunks; ++ch)
+      tma_load_3d(simg + (size_t)ch * t.kc * TC, &tmap, bar, c0, row, ch * t.kc);
+    bulk_load_1d(stab0, grow, tab_bytes, bar);
+  }
+  const bool late = !mbar_wait_bounded(bar, 0, c.err);
+  if (__syncthreads_or(late)) return;
+  const int2 nz = stab0[0];
+  const int2 *stab = stab0 + 1;
+  const float sign = c.out_sign, zero = __fmul_rn(sign, 0.f);
+  const bool rev = c.reverse != 0;
+  for (int i = lo + tid; i < hi; i += blockDim.x) {
+    const int lc = idx[i] - row * c.W - c0;
+    auto pxs = [&](int k) { return biased(simg[(size_t)(rev ? K - 1 - k : k) * TC + lc]); };
+    const float I0 = pxs(0);
+    OutT *o = out + i;
+    for (int j = 0; j < nz.x; ++j, o += n) st_cs(o, zero);
+    if (nz.x < nz.y) {
+      auto evalF = [&](int2 kf) {
+        const float x = pxs(kf.x), y = pxs(kf.x + 1);
+        return __fmaf_rn(__int_as_float(kf.y), __fsub_rn(x, y), __fsub_rn(I0, x));
+      };
+      float Fp = evalF(stab[nz.x]);
+#pragma unroll 4
+      for (int j = nz.x; j < nz.y; ++j, o += n) {
+        const float F = evalF(stab[j + 1]);
+        st_cs(o, __fmul_rn(sign, __fsub_rn(F, Fp)));
+        Fp = F;
+      }
+    }
+    for (int j = max(nz.y, nz.x); j < B; ++j, o += n) st_cs(o, zero);
+  }
+}
 }  // namespace dr

@@ -743,8 +743,32 @@ extern "C" dr_status dr_reconstruct_selected(const dr_plan_t *p, const uint16_t 
     return DR_ERR_INVALID_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  const int blocks = (n + 255) / 256;
   const bool bf16 = p->out_dtype == DR_OUT_BF16;
+  // Staged tiles load every image row segment that holds a listed pixel and
+  // give each thread one pixel; they pay off when most pixels are listed.
+  // Sparse lists take the per-lane walk (images read from global memory).
+  const bool dense = (double)n >= 0.6 * (double)p->rows * p->cols;
+  if (dense && p->kernel == DR_KERNEL_ROWS && p->c.tab && tma_usable(p, img)) {
+    // staged: one CTA per (row, tile) of the plan's launch shape, 256 threads
+    CUtensorMap tm;
+    dr_status s = make_tensor_map(p, img, &tm);
+    if (s != DR_OK) return s;
+    const void *fn = bf16 ? (const void *)selected_rows_kernel<__nv_bfloat16>
+                          : (const void *)selected_rows_kernel<float>;
+    s = allow_smem(fn);
+    if (s != DR_OK) return s;
+    dim3 grid((p->cols + p->tune.tile_cols - 1) / p->tune.tile_cols, p->rows);
+    if (bf16)
+      selected_rows_kernel<__nv_bfloat16><<<grid, 256, p->smem_bytes, st>>>(
+          tm, p->c, p->tune, idx, n, (__nv_bfloat16 *)out);
+    else
+      selected_rows_kernel<float><<<grid, 256, p->smem_bytes, st>>>(tm, p->c, p->tune, idx, n,
+                                                                     (float *)out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("dr_reconstruct_selected", e);
+    return DR_OK;
+  }
+  const int blocks = (n + 255) / 256;
   if (p->geom_prec == DR_GEOM_FP64) {
     if (bf16)
       selected_kernel<GeoF64, __nv_bfloat16><<<blocks, 256, 0, st>>>(
