@@ -44,11 +44,22 @@ FALLBACK_HBM_GBS = 6800.0
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "rows_kernel_full_detector_traffic.txt")
 
 
-def kernel_source_hash():
+ROWS_KERNEL_END = "// ------------------------------------------------- persistent batch kernel ---"
+
+
+def kernel_source_hash(device_src=None, tables_src=None):
+    """Hash of the code the rows kernel is built from: the device header up to
+    the persistent batch kernel (helpers, depth model, row tables, rows_tile,
+    rows_kernel) and the table layouts."""
+    csrc = os.path.join(ROOT, "paper_2201_13309_gb300", "csrc")
+    if device_src is None:
+        device_src = open(os.path.join(csrc, "dr_device.cuh"), "rb").read()
+    if tables_src is None:
+        tables_src = open(os.path.join(csrc, "dr_tables.h"), "rb").read()
+    cut = device_src.find(ROWS_KERNEL_END.encode())
     h = hashlib.sha256()
-    for f in ("dr_device.cuh", "dr_tables.h"):
-        with open(os.path.join(ROOT, "paper_2201_13309_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    h.update(device_src[:cut] if cut >= 0 else device_src)
+    h.update(tables_src)
     return h.hexdigest()[:16]
 
 
