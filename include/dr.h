@@ -53,7 +53,7 @@ typedef enum {
   DR_ERR_UNSUPPORTED = 8    /* valid request outside what this build handles */
 } dr_status;
 
-enum { DR_EDGE_LEADING = 0, DR_EDGE_TRAILING = 1 };
+enum { DR_EDGE_LEADING = 0, DR_EDGE_TRAILING = 1, DR_EDGE_BOTH = 2 };
 enum { DR_OUT_F32 = 0, DR_OUT_BF16 = 1 };
 enum { DR_GEOM_FP32 = 0, DR_GEOM_FP64 = 1 };
 enum { DR_KERNEL_ROWS = 0, DR_KERNEL_PIXELS = 1 };
@@ -63,7 +63,10 @@ enum { DR_KERNEL_ROWS = 0, DR_KERNEL_PIXELS = 1 };
  * radius wire_radius whose axis runs along wire_axis through each wire centre.
  * edge selects the wire edge whose passage is reconstructed: the leading edge
  * (the one moving in the direction of travel; a pixel's intensity drops as it
- * covers a scatterer) or the trailing edge (intensity comes back). */
+ * covers a scatterer), the trailing edge (intensity comes back), or
+ * DR_EDGE_BOTH, the mean of the two reconstructions.  The direction of travel
+ * is that of the whole scan (first to last wire centre); a path that turns
+ * back along the beam is reconstructed run by run with that same edge. */
 typedef struct {
   double beam_origin[3];
   double beam_dir[3];
@@ -103,6 +106,8 @@ typedef struct {
                                of projected depth (FP32 geometry) */
   int32_t row_tables;       /* 1: the per-row (k, f) tables were built once at
                                plan time; 0: each tile builds its own */
+  int32_t parts;            /* launches per reconstruction: monotone runs of
+                               the wire path x wire edges (1 for most scans) */
   double depth_min, depth_max;   /* range of all d_k (mm) */
   double min_step;               /* smallest |d_{k+1} - d_k| (mm) */
   size_t device_bytes;           /* device memory held by the plan */
@@ -112,7 +117,9 @@ typedef struct {
 
 /* Build a plan: validate the geometry, compute the per-pixel (or per-row,
  * when all pixels of a row share their depths) constants in FP64, check that
- * every depth sequence is strictly monotone, upload the constants and pick the
+ * every depth sequence is strictly monotone within each run of the wire path
+ * (the path may turn back along the beam; two consecutive centres at the same
+ * position along the beam are rejected), upload the constants and pick the
  * kernel and tile shape.
  *   wire_centres  host [K][3] FP64, K >= 2
  *   bin_edges     host [B+1] FP64 strictly increasing (depth, mm), B >= 1

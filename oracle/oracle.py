@@ -146,8 +146,12 @@ def reconstruct(geom, wires, images, edges, edge="leading", r0=0, nrows=None,
                 threads=None):
     """FP64 reconstruction of rows r0 .. r0+nrows-1: [B, nrows, cols].
 
-    ``images`` is the whole ROI stack [K, rows, cols] (uint16).
+    ``images`` is the whole ROI stack [K, rows, cols] (uint16).  edge "both"
+    is the mean of the leading- and trailing-edge reconstructions.
     """
+    if edge == "both":
+        return 0.5 * (reconstruct(geom, wires, images, edges, "leading", r0, nrows, threads)
+                      + reconstruct(geom, wires, images, edges, "trailing", r0, nrows, threads))
     lib = _load()
     H, W = geom["rows"], geom["cols"]
     nrows = H - r0 if nrows is None else nrows

@@ -82,10 +82,10 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
       set_error("dr_batch_create: job %d has no plan", i);
       return DR_ERR_INVALID_ARG;
     }
-    if (p->kernel != DR_KERNEL_ROWS || p->geom_prec != DR_GEOM_FP32 || p->cols % 8 != 0 ||
-        p->tune.ppt != 4) {
-      set_error("dr_batch_create: job %d: the batch runs the rows kernel with FP32 geometry "
-                "on widths that are multiples of 8", i);
+    if (!p->parts.empty() || p->kernel != DR_KERNEL_ROWS || p->geom_prec != DR_GEOM_FP32 ||
+        p->cols % 8 != 0 || p->tune.ppt != 4) {
+      set_error("dr_batch_create: job %d: the batch runs single-run, single-edge rows-kernel "
+                "plans with FP32 geometry on widths that are multiples of 8", i);
       return DR_ERR_UNSUPPORTED;
     }
     if (out_dtype >= 0 && p->out_dtype != out_dtype) {

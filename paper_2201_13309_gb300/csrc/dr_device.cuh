@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -244,6 +245,25 @@ __device__ __forceinline__ void store_px(OutT *p, const float (&v)[PPT]) {
   }
 }
 
+__device__ __forceinline__ float out_load(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ float out_load(const __nv_bfloat16 *p) {
+  return __bfloat162float(*p);
+}
+
+template <class OutT, int PPT>
+__device__ __forceinline__ void load_out_px(const OutT *p, float (&v)[PPT]) {
+  if constexpr (PPT == 4 && sizeof(OutT) == 4) {
+    const float4 u = __ldcs(reinterpret_cast<const float4 *>(p));
+    v[0] = u.x;
+    v[1] = u.y;
+    v[2] = u.z;
+    v[3] = u.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) v[i] = out_load(p + i);
+  }
+}
+
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Stage the image tile [K][1][tile_cols] (row `row`, columns c0..) into
@@ -391,6 +411,7 @@ __device__ __forceinline__ bool rows_tile(const CUtensorMap *tmap, const uint16_
   const float sign = c.out_sign;
   const size_t plane = (size_t)c.H * c.W;
   OutT *const o0 = out + (size_t)row * c.W + col;
+  const bool acc = c.accumulate != 0;
   float zero[PPT];
 #pragma unroll
   for (int i = 0; i < PPT; ++i) zero[i] = __fmul_rn(sign, 0.f);
@@ -399,8 +420,10 @@ __device__ __forceinline__ bool rows_tile(const CUtensorMap *tmap, const uint16_
 #pragma unroll 4
     for (int j = a; j < b; ++j, o += plane) store_px<OutT, PPT>(o, zero);
   };
-  zero_fill(slice_lo(0, nz_lo), slice_hi(0, nz_lo));
-  zero_fill(slice_lo(nz_hi, B), slice_hi(nz_hi, B));
+  if (!acc) {  // bins without data: written as zero (nothing to add when accumulating)
+    zero_fill(slice_lo(0, nz_lo), slice_hi(0, nz_lo));
+    zero_fill(slice_lo(nz_hi, B), slice_hi(nz_hi, B));
+  }
 
   const int a = slice_lo(nz_lo, nz_hi), b = slice_hi(nz_lo, nz_hi);
   if (a >= b) return true;
@@ -417,20 +440,34 @@ __device__ __forceinline__ bool rows_tile(const CUtensorMap *tmap, const uint16_
     for (int i = 0; i < PPT; ++i)
       F[i] = __fmaf_rn(f, __fsub_rn(x[i], y[i]), __fsub_rn(I0[i], x[i]));
   };
-  float Fp[PPT];
-  evalF(stab[a], Fp);
-  OutT *o = o0 + (size_t)a * plane;
+  // the data range; the accumulating form adds to what is there
+  auto stream = [&](auto add) {
+    constexpr bool kAdd = decltype(add)::value;
+    float Fp[PPT];
+    evalF(stab[a], Fp);
+    OutT *o = o0 + (size_t)a * plane;
 #pragma unroll 4
-  for (int j = a; j < b; ++j, o += plane) {
-    float Fn[PPT], v[PPT];
-    evalF(stab[j + 1], Fn);
+    for (int j = a; j < b; ++j, o += plane) {
+      float Fn[PPT], v[PPT];
+      evalF(stab[j + 1], Fn);
 #pragma unroll
-    for (int i = 0; i < PPT; ++i) {
-      v[i] = __fmul_rn(sign, __fsub_rn(Fn[i], Fp[i]));
-      Fp[i] = Fn[i];
+      for (int i = 0; i < PPT; ++i) {
+        v[i] = __fmul_rn(sign, __fsub_rn(Fn[i], Fp[i]));
+        Fp[i] = Fn[i];
+      }
+      if constexpr (kAdd) {
+        float old[PPT];
+        load_out_px<OutT, PPT>(o, old);
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) v[i] = __fadd_rn(old[i], v[i]);
+      }
+      store_px<OutT, PPT>(o, v);
     }
-    store_px<OutT, PPT>(o, v);
-  }
+  };
+  if (acc)
+    stream(std::true_type{});
+  else
+    stream(std::false_type{});
   return true;
 }
 
@@ -564,7 +601,8 @@ __global__ void __launch_bounds__(256) pixels_kernel(const __grid_constant__ CUt
     const float f = Geo::frac(e, t0, inv);
     const float F = __fmaf_rn(f, __fsub_rn(Ik, Ik1), __fsub_rn(I0, Ik));
     if (j > 0) {
-      st_cs(o, __fmul_rn(sign, __fsub_rn(F, Fp)));
+      const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
+      st_cs(o, c.accumulate ? __fadd_rn(out_load(o), v) : v);
       o += plane;
     }
     Fp = F;

@@ -6,6 +6,8 @@
 
 #include <cuda.h>
 
+#include <vector>
+
 #include "../../include/dr.h"
 #include "dr_tables.h"
 
@@ -21,6 +23,11 @@ struct dr_plan {
   int threads, smem_bytes;
   size_t device_bytes;
   void *dev_block;         // single device allocation holding every table
+  // composite plans (monotone runs of a back-and-forth scan, both wire
+  // edges): the parts run in order on images + part_k0 planes, the first
+  // writing the output and the others adding to it; empty for a plain plan
+  std::vector<dr_plan *> parts;
+  std::vector<int> part_k0;
 };
 
 namespace dr {
@@ -60,6 +67,9 @@ dr_status build_plan_tables(const dr_plan_t *p, int2 *tab);
 // Load every reconstruction kernel on the current device (module loading is
 // otherwise lazy, at the first launch).
 dr_status preload_kernels();
+// All launches of a plan (the parts of a composite plan in order).
+dr_status launch_plan(const dr_plan_t *p, const uint16_t *img, void *out,
+                      struct CUstream_st *st);
 // Reconstruction launch of a plan (defined with the kernels).
 dr_status launch_reconstruct(const dr_plan_t *p, const uint16_t *img, void *out,
                              struct CUstream_st *st);

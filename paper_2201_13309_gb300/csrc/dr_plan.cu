@@ -124,9 +124,12 @@ void choose_chunks(int K, int tile_cols, int *kc, int *nchunks) {
 
 }  // namespace dr
 
-extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires,
-                             int32_t K, const double *edges, int32_t B,
-                             const dr_plan_options *opt_in, dr_plan_t **out) {
+// One monotone plan.  side != 0 fixes the tangent side s (the wire edge
+// chosen by the whole scan's travel), for the runs of a composite plan whose
+// own travel may point the other way.
+static dr_status plan_one(const dr_geometry *g, const double *wires, int32_t K,
+                          const double *edges, int32_t B, const dr_plan_options *opt_in,
+                          int side, dr_plan_t **out) {
   if (out) *out = nullptr;
   if (!g || !wires || !edges || !out) {
     set_error("dr_plan: null argument");
@@ -144,7 +147,7 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires,
     return DR_ERR_UNSUPPORTED;
   }
   if (g->edge != DR_EDGE_LEADING && g->edge != DR_EDGE_TRAILING) {
-    set_error("dr_plan: edge must be DR_EDGE_LEADING or DR_EDGE_TRAILING");
+    set_error("dr_plan: edge must be DR_EDGE_LEADING, DR_EDGE_TRAILING or DR_EDGE_BOTH");
     return DR_ERR_INVALID_ARG;
   }
   if ((opt.out_dtype != DR_OUT_F32 && opt.out_dtype != DR_OUT_BF16) ||
@@ -209,7 +212,8 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires,
     return DR_ERR_GEOMETRY;
   }
   const bool reverse = travel < 0.0;
-  const double sgn = (reverse ? -1.0 : 1.0) * (g->edge == DR_EDGE_LEADING ? 1.0 : -1.0);
+  const double sgn = side != 0 ? (double)side
+                               : (reverse ? -1.0 : 1.0) * (g->edge == DR_EDGE_LEADING ? 1.0 : -1.0);
   const double sR = sgn * R;
   bool has_eta = false;
   double ymin = yk[0], ymax = yk[0];
@@ -544,8 +548,116 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires,
   return DR_OK;
 }
 
+// The public plan.  A wire path whose projected position along the beam
+// changes direction (a back-and-forth scan) is split into monotone runs that
+// share their turning steps; each run is a plan of its own that keeps the
+// whole scan's wire edge, and the runs' outputs add up (the apportioning is a
+// sum over intervals).  DR_EDGE_BOTH is the mean of the leading- and
+// trailing-edge reconstructions.  Single-run, single-edge scans are one plan.
+extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t K,
+                             const double *edges, int32_t B, const dr_plan_options *opt,
+                             dr_plan_t **out) {
+  if (out) *out = nullptr;
+  if (!g || !wires || !edges || !out) {
+    set_error("dr_plan: null argument");
+    return DR_ERR_INVALID_ARG;
+  }
+  if (K < 2 || B < 1) {
+    set_error("dr_plan: need K >= 2, B >= 1 (K=%d B=%d)", K, B);
+    return DR_ERR_INVALID_ARG;
+  }
+  const bool both = g->edge == DR_EDGE_BOTH;
+  // projected wire position along the beam (the plan's e2 coordinate)
+  std::vector<int> starts{0};
+  double travel = 0.0;
+  {
+    V3 ax = v3(g->wire_axis), bd = v3(g->beam_dir), O = v3(g->beam_origin);
+    if (norm(ax) > 0 && norm(bd) > 0 && finite3(wires) && finite3(wires + 3 * (K - 1))) {
+      ax = (1.0 / norm(ax)) * ax;
+      bd = (1.0 / norm(bd)) * bd;
+      const V3 bp = bd - dot(bd, ax) * ax;
+      if (norm(bp) > 1e-9) {
+        const V3 e2 = (1.0 / norm(bp)) * bp;
+        travel = dot(v3(wires + 3 * (K - 1)) - v3(wires), e2);
+        int dir = 0;
+        for (int k = 0; k + 1 < K && travel != 0.0; ++k) {
+          if (!finite3(wires + 3 * k) || !finite3(wires + 3 * (k + 1))) break;
+          const double dz = dot(v3(wires + 3 * (k + 1)) - v3(wires + 3 * k), e2);
+          if (dz == 0.0) {
+            set_error("dr_plan: wire steps %d and %d at the same position along the beam", k,
+                      k + 1);
+            return DR_ERR_NONMONOTONIC;
+          }
+          const int d = dz > 0 ? 1 : -1;
+          if (dir != 0 && d != dir) starts.push_back(k);  // run turns at step k
+          dir = d;
+        }
+      }
+    }
+  }
+  // a single run (and a wire that does not travel: plan_one reports it)
+  if ((starts.size() == 1 || travel == 0.0) && !both)
+    return plan_one(g, wires, K, edges, B, opt, 0, out);
+  if (travel == 0.0) {
+    set_error("dr_plan: the wire ends where it started along the beam (no travel)");
+    return DR_ERR_GEOMETRY;
+  }
+  dr_plan_t *top = new (std::nothrow) dr_plan_t();
+  if (!top) {
+    set_error("dr_plan: host allocation failed");
+    return DR_ERR_OOM;
+  }
+  const int nedges = both ? 2 : 1;
+  for (int ei = 0; ei < nedges; ++ei) {
+    dr_geometry ge = *g;
+    ge.edge = both ? (ei == 0 ? DR_EDGE_LEADING : DR_EDGE_TRAILING) : g->edge;
+    const int side = (travel > 0 ? 1 : -1) * (ge.edge == DR_EDGE_LEADING ? 1 : -1);
+    for (size_t r = 0; r < starts.size(); ++r) {
+      const int k0 = starts[r];
+      const int k1 = r + 1 < starts.size() ? starts[r + 1] : K - 1;  // inclusive
+      dr_plan_t *part = nullptr;
+      dr_status st = plan_one(&ge, wires + 3 * k0, k1 - k0 + 1, edges, B, opt, side, &part);
+      if (st != DR_OK) {
+        dr_plan_destroy(top);
+        return st;
+      }
+      if (!top->parts.empty()) part->c.accumulate = 1;
+      if (both) part->c.out_sign *= 0.5f;
+      top->parts.push_back(part);
+      top->part_k0.push_back(k0);
+    }
+  }
+  const dr_plan_t *f = top->parts.front();
+  top->rows = f->rows;
+  top->cols = f->cols;
+  top->K = K;
+  top->B = B;
+  top->edge = g->edge;
+  top->kernel = f->kernel;
+  top->out_dtype = f->out_dtype;
+  top->geom_prec = f->geom_prec;
+  top->shift = f->shift;
+  top->nb = f->nb;
+  top->depth_min = 1e300;
+  top->depth_max = -1e300;
+  top->min_step = 1e300;
+  for (const dr_plan_t *q : top->parts) {
+    top->depth_min = std::min(top->depth_min, q->depth_min);
+    top->depth_max = std::max(top->depth_max, q->depth_max);
+    top->min_step = std::min(top->min_step, q->min_step);
+    top->device_bytes += q->device_bytes;
+  }
+  top->c = f->c;
+  top->tune = f->tune;
+  top->threads = f->threads;
+  top->smem_bytes = f->smem_bytes;
+  *out = top;
+  return DR_OK;
+}
+
 extern "C" void dr_plan_destroy(dr_plan_t *p) {
   if (!p) return;
+  for (dr_plan_t *q : p->parts) dr_plan_destroy(q);
   if (p->dev_block) cudaFree(p->dev_block);
   delete p;
 }
@@ -576,6 +688,7 @@ extern "C" dr_status dr_plan_get_info(const dr_plan_t *p, dr_plan_info *info) {
   info->reversed = p->c.reverse;
   info->fixed_shift = p->shift;
   info->row_tables = p->c.tab != nullptr;
+  info->parts = p->parts.empty() ? 1 : (int32_t)p->parts.size();
   info->depth_min = p->depth_min;
   info->depth_max = p->depth_max;
   info->min_step = p->min_step;

@@ -204,6 +204,18 @@ dr_status launch_reconstruct(const dr_plan_t *p, const uint16_t *img, void *out,
               : dispatch_out<GeoFx, float>(p, tma, tm, img, out, st);
 }
 
+// A plan's launches: one, or each part of a composite plan on its run's image
+// planes (part 0 writes the output, later parts add to it).
+dr_status launch_plan(const dr_plan_t *p, const uint16_t *img, void *out, cudaStream_t st) {
+  if (p->parts.empty()) return launch_reconstruct(p, img, out, st);
+  const size_t plane = (size_t)p->rows * p->cols;
+  for (size_t i = 0; i < p->parts.size(); ++i) {
+    dr_status s = launch_reconstruct(p->parts[i], img + (size_t)p->part_k0[i] * plane, out, st);
+    if (s != DR_OK) return s;
+  }
+  return DR_OK;
+}
+
 }  // namespace dr
 
 using namespace dr;
@@ -226,7 +238,7 @@ extern "C" dr_status dr_reconstruct(const dr_plan_t *p, const uint16_t *img, voi
     return DR_ERR_INVALID_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  dr_status s = launch_reconstruct(p, img, out, st);
+  dr_status s = launch_plan(p, img, out, st);
   if (s != DR_OK) return s;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail("dr_reconstruct: launch", e);
@@ -279,6 +291,10 @@ extern "C" dr_status dr_plan_depths(const dr_plan_t *p, int32_t r0, int32_t nrow
   if (!p || r0 < 0 || nrows < 0 || r0 + nrows > p->rows) {
     set_error("dr_plan_depths: bad arguments");
     return DR_ERR_INVALID_ARG;
+  }
+  if (!p->parts.empty()) {
+    set_error("dr_plan_depths: not available for plans of several runs or both edges");
+    return DR_ERR_UNSUPPORTED;
   }
   const long long n = (long long)nrows * p->cols * p->K;
   if (n == 0) return DR_OK;
@@ -509,14 +525,20 @@ extern "C" dr_status dr_reconstruct_streamed(const dr_plan_t *p, const uint16_t 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->comp, ss->up_done[b], 0);
     if (e == cudaSuccess && i >= nbuf) e = cudaStreamWaitEvent(ss->comp, ss->down_done[b], 0);
     if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: upload", e);
-    dr_plan_t slab = *p;
-    slab.rows = n;
-    slab.c.H = n;
-    slab.c.grp = p->c.grp + (size_t)r0 * groups_per_row;
-    slab.c.grp64 = p->c.grp64 + (size_t)r0 * groups_per_row;
-    if (p->c.tab) slab.c.tab = p->c.tab + (size_t)r0 * p->c.tab_stride;
-    s = launch_reconstruct(&slab, dimg, dout, ss->comp);
-    if (s != DR_OK) return s;
+    const size_t nparts = p->parts.empty() ? 1 : p->parts.size();
+    for (size_t q = 0; q < nparts; ++q) {
+      const dr_plan_t *part = p->parts.empty() ? p : p->parts[q];
+      const int k0 = p->parts.empty() ? 0 : p->part_k0[q];
+      dr_plan_t slab = *part;
+      slab.parts.clear();
+      slab.rows = n;
+      slab.c.H = n;
+      slab.c.grp = part->c.grp + (size_t)r0 * groups_per_row;
+      slab.c.grp64 = part->c.grp64 + (size_t)r0 * groups_per_row;
+      if (part->c.tab) slab.c.tab = part->c.tab + (size_t)r0 * part->c.tab_stride;
+      s = launch_reconstruct(&slab, dimg + (size_t)k0 * n * W, dout, ss->comp);
+      if (s != DR_OK) return s;
+    }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(ss->comp_done[b], ss->comp);
     // download the slab's bins into rows r0.. of every output plane
@@ -736,6 +758,10 @@ extern "C" dr_status dr_reconstruct_selected(const dr_plan_t *p, const uint16_t 
   if (!p || n < 0) {
     set_error("dr_reconstruct_selected: bad arguments");
     return DR_ERR_INVALID_ARG;
+  }
+  if (!p->parts.empty()) {
+    set_error("dr_reconstruct_selected: not available for plans of several runs or both edges");
+    return DR_ERR_UNSUPPORTED;
   }
   if (n == 0 || (size_t)p->rows * p->cols == 0) return DR_OK;
   if (!img || !idx || !out) {

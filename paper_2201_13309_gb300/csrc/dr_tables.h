@@ -77,6 +77,9 @@ struct Consts {
   // for edge j = 0..B.
   const int2 *tab;
   int tab_stride;
+  // 1: add this plan's bins to the output instead of writing them (the later
+  // parts of a composite plan: monotone runs, both wire edges)
+  int accumulate;
 };
 
 // Entries of one row table: a header, B + 1 edges, rounded up to an even

@@ -20,7 +20,7 @@ DR_OK = 0
 STATUS = {0: "DR_OK", 1: "DR_ERR_INVALID_ARG", 2: "DR_ERR_GEOMETRY",
           3: "DR_ERR_NONMONOTONIC", 4: "DR_ERR_OOM", 5: "DR_ERR_BUDGET",
           6: "DR_ERR_CUDA", 7: "DR_ERR_TIMEOUT", 8: "DR_ERR_UNSUPPORTED"}
-EDGES = {"leading": 0, "trailing": 1}
+EDGES = {"leading": 0, "trailing": 1, "both": 2}
 OUT_DTYPES = {"f32": 0, "bf16": 1}
 GEOM_PRECISIONS = {"fp32": 0, "fp64": 1}
 KERNELS = {0: "rows", 1: "pixels"}
@@ -57,7 +57,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "rows", "cols", "K", "B", "kernel", "tile_cols", "pixels_per_thread",
         "bin_groups", "threads", "smem_bytes", "tma_chunk", "tma_chunks", "out_dtype",
-        "geom_precision", "edge", "reversed", "fixed_shift", "row_tables")] + [
+        "geom_precision", "edge", "reversed", "fixed_shift", "row_tables", "parts")] + [
         ("depth_min", ctypes.c_double), ("depth_max", ctypes.c_double),
         ("min_step", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
         ("bytes_per_call", ctypes.c_double)]

@@ -108,6 +108,44 @@ def test_edges_and_reversed_travel(edge):
     assert_parity(out.cpu().numpy(), ref_of(back, edge), back.images)
 
 
+def back_and_forth(n_up=24, n_down=10, n_up2=14):
+    """Wire path along +z, back along -z, and on again (steps of 1 um)."""
+    a = synth.wire_path(n_up)
+    b = synth.wire_path(n_down + 1, z0=a[-1, 2], dz=-0.001)[1:]
+    c = synth.wire_path(n_up2 + 1, z0=b[-1, 2], dz=0.001)[1:]
+    return np.concatenate([a, b, c])
+
+
+@pytest.mark.parametrize("edge", ["leading", "trailing", "both"])
+@pytest.mark.parametrize("rotate", [0.0, 6.0])
+def test_back_and_forth_wire_and_both_edges(edge, rotate):
+    wires = back_and_forth()
+    geom = synth.detector_geometry(12, 64, roi_origin=(26, 0), det_rows=64, det_cols=64,
+                                   rotate_deg=rotate)
+    rng = np.random.Generator(np.random.PCG64(81))
+    scat = synth.tiny_scatterers(rng, 4)
+    images = synth.poisson_u16(rng, synth.expected_counts(geom, wires, scat))
+    sc = synth.Scan(geom, wires, synth.bin_edges(-40, 60, 1.0), images)
+    plan, out = run(sc, edge=edge)
+    info = plan.info()
+    assert info["parts"] == 3 * (2 if edge == "both" else 1)
+    assert info["kernel"] == ("pixels" if rotate else "rows")
+    assert_parity(out.cpu().numpy(), ref_of(sc, edge), sc.images)
+
+
+def test_both_edges_monotone_and_streamed():
+    sc = synth.tiny_scan(82, rows=20, cols=64, K=41)
+    plan, out = run(sc, edge="both")
+    assert plan.info()["parts"] == 2
+    assert_parity(out.cpu().numpy(), ref_of(sc, "both"), sc.images)
+    h_img = torch.from_numpy(sc.images.view(np.int16)).pin_memory()
+    h_out = torch.empty((sc.B, 20, 64)).pin_memory()
+    ws = torch.empty(3 << 20, dtype=torch.uint8, device="cuda")
+    plan.reconstruct_streamed(h_img, h_out, ws, slab_rows=3)
+    torch.cuda.synchronize()
+    assert torch.equal(h_out.view(torch.int32), out.cpu().view(torch.int32))
+
+
 @pytest.mark.parametrize("H,W,K,lo,hi,w", [(5, 200, 37, -30, 30, 0.5),
                                            (3, 136, 9, -8, 8, 2.0),
                                            (7, 260, 51, -45, 45, 1.0),
