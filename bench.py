@@ -717,6 +717,9 @@ def main():
     ap.add_argument("--tile-cols", type=int, default=0, help="fixed tile width (0: autotune)")
     ap.add_argument("--bin-groups", type=int, default=0)
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
+    ap.add_argument("--rotate", type=float, default=0.0,
+                    help="rotate the detector in its plane (degrees): per-pixel depths")
+    ap.add_argument("--tilt", type=float, default=0.0, help="tilt the detector about x (degrees)")
     ap.add_argument("--rows", type=int, default=2048,
                     help="reconstruct only the first ROWS detector rows (small profiling case)")
     args = ap.parse_args()
@@ -760,6 +763,9 @@ def main():
         return 0
 
     spec = synth.full_scan_spec(0)
+    if args.rotate or args.tilt:
+        spec.geom = synth.detector_geometry(2048, 2048, rotate_deg=args.rotate,
+                                            tilt_deg=args.tilt)
     if args.rows != spec.geom["rows"]:
         spec.geom = dict(spec.geom, rows=args.rows)
         keep = spec.scat.spot_row < args.rows - 2
@@ -827,10 +833,12 @@ def main():
     peak, peak_kind = measured_hbm_peak()
     alg_bytes = info["bytes_per_call"]
     achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic() if info["kernel"] == "rows" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "peak_kind": peak_kind, "kernel": "rows_kernel<GeoFx,float,tma,4>",
+                "peak_kind": peak_kind,
+                "kernel": ("rows_kernel<GeoFx,float,tma,4>" if info["kernel"] == "rows"
+                           else "pixels_kernel<GeoFx,float,tma>"),
                 "algorithmic_bytes_per_launch": alg_bytes}
 
     # end to end through the public API with host buffers: the streamed form
@@ -898,8 +906,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.rows == 2048 else
-                       WORKLOAD + f" (first {args.rows} rows only)", "pixels": P, "wire_steps": spec.K,
+            "config": {"workload": (WORKLOAD if args.rows == 2048 else
+                                    WORKLOAD + f" (first {args.rows} rows only)")
+                       + (f"; detector rotated {args.rotate} deg, tilted {args.tilt} deg"
+                          if args.rotate or args.tilt else ""), "pixels": P, "wire_steps": spec.K,
                        "bins": spec.B, "parallelism": f"replicas x{world}",
                        "l2": f"input ({2 * units_per_step / 1e9:.2f} GB) and output "
                              f"({4 * P * spec.B / 1e9:.1f} GB) larger than L2; no flush",

@@ -541,71 +541,167 @@ __global__ void __launch_bounds__(512, 1) batch_rows_kernel(const BatchScan *__r
 }
 
 // ------------------------------------------------------- pixels kernel ---
+// General geometry: every pixel has its own depth sequence.  A CTA owns one
+// row x tile_cols pixels x all steps; its warps are (slab, share) pairs: a
+// slab is 32 adjacent pixels (lane = pixel), and the bin_groups shares of a
+// slab split its bins.
+//  1. All threads evaluate the tile's K x tile_cols depth positions into
+//     shared memory (thread (pixel, share) takes steps share, share + G, ...)
+//     while the TMA copies the image tile.
+//  2. One warp per slab finds the slab's data span [jlo, jhi): bin j can
+//     hold data for some pixel only if e_{j+1} > min d_0 and e_j < max
+//     d_{K-1}.
+//  3. Every share gets an equal part of the span, which it walks (binary
+//     search of its first step, then bins and steps together), and an equal
+//     part of the bins outside it, which are zero.  The bin loop is uniform
+//     over the warp, so the 32 lanes store bin j as one coalesced line.
+// A bin is zero for a pixel when e_{j+1} <= d_0 or e_j >= d_{K-1}, the same
+// rule as the rows kernel's, so both kernels give bitwise the same bins.
+// Shared-memory layout: [0, 128) mbarrier and the slab spans, then the image
+// tile [Kpad][tile_cols] uint16, the depth positions [K][tile_cols], the bin
+// edges [B + 1].
+template <class T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
+template <class T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
 
 template <class Geo, class OutT, bool kTma>
-__global__ void __launch_bounds__(256) pixels_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                     const uint16_t *__restrict__ img,
-                                                     OutT *__restrict__ out, const Consts c,
-                                                     const Tuning t) {
+__global__ void __launch_bounds__(1024) pixels_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                         const uint16_t *__restrict__ img,
+                                                         OutT *__restrict__ out, const Consts c,
+                                                         const Tuning t) {
   using pos_t = typename Geo::pos_t;
-  using step_t = typename Geo::step_t;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  int2 *span = reinterpret_cast<int2 *>(smem + 16);  // per slab, at most 8 slabs
   uint16_t *simg = reinterpret_cast<uint16_t *>(smem + 128);
-  const int TC = t.tile_cols, K = c.K, B = c.B;
+  const int TC = t.tile_cols, K = c.K, B = c.B, G = t.bin_groups;
   const int Kpad = t.kc * t.nchunks;
-  step_t *sstep = reinterpret_cast<step_t *>(smem + 128 + align16((size_t)Kpad * TC * 2));
-  pos_t *sedge = reinterpret_cast<pos_t *>(reinterpret_cast<unsigned char *>(sstep) +
-                                           align16((size_t)K * sizeof(step_t)));
+  pos_t *spos = reinterpret_cast<pos_t *>(smem + 128 + align16((size_t)Kpad * TC * 2));
+  pos_t *sedge = reinterpret_cast<pos_t *>(reinterpret_cast<unsigned char *>(spos) +
+                                           align16((size_t)K * TC * sizeof(pos_t)));
   const int row = blockIdx.y, c0 = blockIdx.x * TC;
   const int tid = threadIdx.x, NT = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nslab = TC >> 5;
+  const int slab = warp % nslab, share = warp / nslab;
+  const int lc = slab * 32 + lane;
+  const int ncols = min(TC, c.W - c0);
+  const bool valid = lc < ncols;
 
   if constexpr (kTma) {
     if (tid == 0) mbar_init(bar, 1);
   }
   stage_tile<kTma>(&tmap, img, simg, bar, c, t, row, c0);
-  const step_t *gsteps = Geo::steps(c);
-  for (int k = tid; k < K; k += NT) sstep[k] = gsteps[k];
+  if (valid) {
+    const auto g = Geo::group(c, row * c.W + c0 + lc);
+    const auto *gsteps = Geo::steps(c);
+    for (int k = share; k < K; k += G) spos[k * TC + lc] = Geo::depth(g, gsteps[k], c);
+  }
   for (int j = tid; j <= B; j += NT) sedge[j] = Geo::edge(c, j);
+  __syncthreads();  // also makes the mbarrier initialisation visible
+  auto pos = [&](int k) { return spos[k * TC + lc]; };
+  if (share == 0) {
+    const pos_t lo_d = warp_min(valid ? pos(0) : sedge[B]);
+    const pos_t hi_d = warp_max(valid ? pos(K - 1) : sedge[0]);
+    int lo = 0, hi = B;
+    while (lo < hi) {  // first j with e_{j+1} > min d_0
+      const int mid = (lo + hi) >> 1;
+      if (sedge[mid + 1] > lo_d) hi = mid; else lo = mid + 1;
+    }
+    const int jlo = lo;
+    hi = B;
+    while (lo < hi) {  // first j with e_j >= max d_{K-1}
+      const int mid = (lo + hi) >> 1;
+      if (sedge[mid] < hi_d) lo = mid + 1; else hi = mid;
+    }
+    if (lane == 0) span[slab] = make_int2(jlo, lo);
+  }
   __syncthreads();
   if constexpr (kTma) {
     if (!mbar_wait_bounded(bar, 0, c.err)) return;
   }
-  const int col = c0 + tid;
-  if (col >= c.W) return;
-  const auto g = Geo::group(c, row * c.W + col);
+  if (!valid) return;
+  const int2 sp = span[slab];
+  const float sign = c.out_sign, zero = __fmul_rn(sign, 0.f);
+  const size_t plane = (size_t)c.H * c.W;
+  const bool acc = c.accumulate != 0;
+  OutT *const o0 = out + (size_t)row * c.W + c0 + lc;
+  // this share's part of the bins outside the span
+  if (!acc) {
+    const int nz = B - (sp.y - sp.x);
+    const int ib = (int)((long long)nz * share / G), ie = (int)((long long)nz * (share + 1) / G);
+    OutT *o = o0 + (size_t)ib * plane;  // [ib, ie) below the span: bins ib..
+    for (int i = ib; i < min(ie, sp.x); ++i, o += plane) st_cs(o, zero);
+    const int ia = max(ib, sp.x);       // the rest above it: bins i - jlo + jhi
+    o = o0 + (size_t)(ia - sp.x + sp.y) * plane;
+    for (int i = ia; i < ie; ++i, o += plane) st_cs(o, zero);
+  }
+  // this share's part of the span
+  const int nd = sp.y - sp.x;
+  const int jb = sp.x + (int)((long long)nd * share / G);
+  const int je = sp.x + (int)((long long)nd * (share + 1) / G);
+  if (jb >= je) return;
+  const pos_t tfirst = pos(0), tlast = pos(K - 1);
   const bool rev = c.reverse != 0;
-  auto spx = [&](int k) { return biased(simg[(size_t)(rev ? K - 1 - k : k) * TC + tid]); };
-
-  // lockstep merge-walk: every lane handles bin edge j together, each with
-  // its own step pointer k (t0 = d_k, t1 = d_{k+1})
-  int k = 0;
-  pos_t t0 = Geo::depth(g, sstep[0], c), t1 = Geo::depth(g, sstep[1], c);
+  auto spx = [&](int k) { return biased(simg[(size_t)(rev ? K - 1 - k : k) * TC + lc]); };
+  // k = last step below e_jb, clamped to an interval
+  pos_t e0 = sedge[jb];
+  int lo = 0, hi = K;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (pos(mid) < e0) lo = mid + 1; else hi = mid;
+  }
+  int k = min(max(lo - 1, 0), K - 2);
+  pos_t t0 = pos(k), t1 = pos(k + 1);
   auto inv = Geo::inv_len(t0, t1);
   const float I0 = spx(0);
-  float Ik = I0, Ik1 = spx(1);
-  const float sign = c.out_sign;
-  const size_t plane = (size_t)c.H * c.W;
-  OutT *o = out + (size_t)row * c.W + col;
-  float Fp = 0.f;
-  for (int j = 0; j <= B; ++j) {
-    const pos_t e = sedge[j];
+  float Ik1 = spx(k + 1);
+  float base = __fsub_rn(I0, spx(k)), dI = __fsub_rn(spx(k), Ik1);
+  // F at edge e (k moves forward only): F = f (I_k - I_{k+1}) + (I_0 - I_k)
+  auto F_at = [&](pos_t e) {
     while (k < K - 2 && t1 < e) {
       ++k;
       t0 = t1;
-      t1 = Geo::depth(g, sstep[k + 1], c);
+      t1 = pos(k + 1);
       inv = Geo::inv_len(t0, t1);
-      Ik = Ik1;
+      const float Ik = Ik1;
       Ik1 = spx(k + 1);
+      base = __fsub_rn(I0, Ik);
+      dI = __fsub_rn(Ik, Ik1);
     }
-    const float f = Geo::frac(e, t0, inv);
-    const float F = __fmaf_rn(f, __fsub_rn(Ik, Ik1), __fsub_rn(I0, Ik));
-    if (j > 0) {
+    return __fmaf_rn(Geo::frac(e, t0, inv), dI, base);
+  };
+  float Fp = F_at(e0);
+  OutT *o = o0 + (size_t)jb * plane;
+  if (acc) {
+    for (int j = jb; j < je; ++j, o += plane) {
+      const pos_t e1 = sedge[j + 1];
+      const float F = F_at(e1);
       const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
-      st_cs(o, c.accumulate ? __fadd_rn(out_load(o), v) : v);
-      o += plane;
+      if (e1 > tfirst && e0 < tlast) st_cs(o, __fadd_rn(out_load(o), v));
+      Fp = F;
+      e0 = e1;
     }
-    Fp = F;
+  } else {
+    // below d_0 both edges give F = 0 exactly, so only the upper test is
+    // needed for the zero rule
+#pragma unroll 2
+    for (int j = jb; j < je; ++j, o += plane) {
+      const pos_t e1 = sedge[j + 1];
+      const float F = F_at(e1);
+      const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
+      st_cs(o, e0 < tlast ? v : zero);
+      Fp = F;
+      e0 = e1;
+    }
   }
 }
 

@@ -89,9 +89,9 @@ int rows_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64) {
 
 int pixels_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64) {
   size_t s = 128;
-  s += align_up((size_t)Kpad * tile_cols * 2, 16);
-  s += align_up((size_t)K * 16, 16);                       // step constants
-  s += align_up((size_t)(B + 1) * (f64 ? 8 : 4), 16);      // edges
+  s += align_up((size_t)Kpad * tile_cols * 2, 16);                 // image tile
+  s += align_up((size_t)K * tile_cols * (f64 ? 8 : 4), 16);        // depth positions
+  s += align_up((size_t)(B + 1) * (f64 ? 8 : 4), 16);              // edges
   return (int)s;
 }
 
@@ -435,22 +435,27 @@ static dr_status plan_one(const dr_geometry *g, const double *wires, int32_t K,
     t.bin_groups = bg;
     p->threads = lanes * bg;
   } else {
+    // per-pixel kernel: tile_cols pixels (slabs of 32) x bin_groups shares
     t.ppt = 1;
-    int tc = opt.tile_cols;
-    if (tc == 0) {
-      tc = 128;
-      int wr = (W + 31) / 32 * 32;
-      if (wr < tc) tc = std::max(wr, 32);
-      while (tc > 32 && 2 * (smem_for(tc) + 1024) > kSmemPerSm) tc /= 2;
-    }
+    int tc = opt.tile_cols == 0 ? 32 : opt.tile_cols;
     if (tc % 32 != 0 || tc > 256) {
       delete p;
-      set_error("dr_plan: per-pixel tile_cols must be a multiple of 32 up to 256");
+      set_error("dr_plan: per-pixel tile_cols must be a multiple of 32 in [32, 256]");
       return DR_ERR_INVALID_ARG;
     }
     t.tile_cols = tc;
-    t.bin_groups = 1;
-    p->threads = tc;
+    int bg = opt.bin_groups;
+    if (bg == 0) {
+      bg = std::max(1, 1024 / tc);
+      while (bg > 1 && B / bg < 16) bg /= 2;
+    }
+    if (bg < 1 || tc * bg > 1024) {
+      delete p;
+      set_error("dr_plan: per-pixel tile_cols x bin_groups must be at most 1024");
+      return DR_ERR_INVALID_ARG;
+    }
+    t.bin_groups = bg;
+    p->threads = tc * bg;
   }
   choose_chunks(K, t.tile_cols, &t.kc, &t.nchunks);
   if (t.kc < 1 || t.kc > 256 || ((size_t)t.kc * t.tile_cols * 2) % 128 != 0) {

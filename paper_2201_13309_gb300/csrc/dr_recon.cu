@@ -9,9 +9,10 @@
 //                 pair, and then streams the bins: per pixel and edge
 //                 F_j = S_k + f_j * dI_k with S_k = I_0 - I_k, dI_k = I_k -
 //                 I_{k+1} (exact in FP32), out_j = F_{j+1} - F_j.
-//  pixels_kernel  every pixel has its own depth sequence; each lane walks its
-//                 steps and the bins in lockstep with the other lanes
-//                 (merge-walk), evaluating depths as it goes.
+//  pixels_kernel  every pixel has its own depth sequence: the tile's depth
+//                 positions go to shared memory once, then the warps split
+//                 the bins evenly and each lane walks its pixel's steps and
+//                 bins together (merge-walk).
 //
 // F is the running sum of the differences, linearly interpolated in depth
 // between step depths, so F_{j+1} - F_j equals the sum over intervals of
