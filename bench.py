@@ -41,22 +41,25 @@ WORKLOAD = ("plain method, full detector: 2048x2048 uint16 pixels, 401 wire step
             "1001 bins of 1 um over [-500,500] um, FP32 output [1001][2048][2048], "
             "device-resident input")
 FALLBACK_HBM_GBS = 6800.0
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "rows_kernel_full_detector_traffic.txt")
-
-
+PROFILE_TRAFFIC = {
+    "rows": os.path.join(ROOT, "profiles", "rows_kernel_full_detector_traffic.txt"),
+    "pixels": os.path.join(ROOT, "profiles", "pixels_kernel_rotated_detector_traffic.txt"),
+}
+# the rows kernel's code ends where the persistent batch kernel begins
 ROWS_KERNEL_END = "// ------------------------------------------------- persistent batch kernel ---"
 
 
-def kernel_source_hash(device_src=None, tables_src=None):
-    """Hash of the code the rows kernel is built from: the device header up to
-    the persistent batch kernel (helpers, depth model, row tables, rows_tile,
-    rows_kernel) and the table layouts."""
+def kernel_source_hash(kernel="rows", device_src=None, tables_src=None):
+    """Hash of the code a kernel is built from: for the rows kernel the device
+    header up to the persistent batch kernel (helpers, depth model, row
+    tables, rows_tile, rows_kernel), for the per-pixel kernel the whole device
+    header; both with the table layouts."""
     csrc = os.path.join(ROOT, "paper_2201_13309_gb300", "csrc")
     if device_src is None:
         device_src = open(os.path.join(csrc, "dr_device.cuh"), "rb").read()
     if tables_src is None:
         tables_src = open(os.path.join(csrc, "dr_tables.h"), "rb").read()
-    cut = device_src.find(ROWS_KERNEL_END.encode())
+    cut = device_src.find(ROWS_KERNEL_END.encode()) if kernel == "rows" else -1
     h = hashlib.sha256()
     h.update(device_src[:cut] if cut >= 0 else device_src)
     h.update(tables_src)
@@ -72,16 +75,16 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic():
+def profiled_traffic(kernel="rows"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
     try:
         kv = {}
-        for line in open(PROFILE_TRAFFIC):
+        for line in open(PROFILE_TRAFFIC[kernel]):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_sha") != kernel_source_hash():
+        if kv.get("kernel_source_sha") != kernel_source_hash(kernel):
             return None
         return float(kv["dram_bytes_per_launch"])
     except Exception:
@@ -833,7 +836,7 @@ def main():
     peak, peak_kind = measured_hbm_peak()
     alg_bytes = info["bytes_per_call"]
     achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
-    traffic = profiled_traffic() if info["kernel"] == "rows" else None
+    traffic = profiled_traffic(info["kernel"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": peak_kind,

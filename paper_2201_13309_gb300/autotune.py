@@ -15,7 +15,7 @@ import threading
 from . import dr
 
 ROWS_CANDIDATES = ((128, 16), (128, 8), (256, 8), (256, 4), (64, 16), (128, 4))
-PIXELS_CANDIDATES = ((32, 32), (32, 16), (32, 8), (64, 16), (64, 8))
+PIXELS_CANDIDATES = ((32, 16), (16, 32), (16, 16), (8, 64), (32, 8), (64, 8))
 
 _lock = threading.Lock()
 

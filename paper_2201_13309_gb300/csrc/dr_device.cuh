@@ -117,6 +117,27 @@ __device__ __forceinline__ void st_cs4(__nv_bfloat16 *p, float a, float b, float
   asm volatile("st.global.cs.v2.b32 [%0], {%1, %2};" ::"l"(p), "r"(ul), "r"(uh) : "memory");
 }
 
+__device__ __forceinline__ void st_cs_u4(void *p, uint4 v) {
+  asm volatile("st.global.cs.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w)
+               : "memory");
+}
+// 16 bytes of the output type's encoding of v (v is +0 or -0 here)
+template <class OutT>
+__device__ __forceinline__ uint4 zero_bits(float v);
+template <>
+__device__ __forceinline__ uint4 zero_bits<float>(float v) {
+  const uint32_t b = __float_as_uint(v);
+  return make_uint4(b, b, b, b);
+}
+template <>
+__device__ __forceinline__ uint4 zero_bits<__nv_bfloat16>(float v) {
+  __nv_bfloat16 h = __float2bfloat16_rn(v);
+  const uint32_t u = *reinterpret_cast<unsigned short *>(&h);
+  const uint32_t b = u | (u << 16);
+  return make_uint4(b, b, b, b);
+}
+
 // --------------------------------------------------------- depth model ---
 
 // FP32 depth position of (group, step) in fixed point (see dr_internal.h).
@@ -138,6 +159,77 @@ __device__ __forceinline__ int32_t depth_fx(const GroupC &g, const StepC &s, con
   return (int32_t)((uint32_t)s.zfx + (uint32_t)g.Q0fx + (uint32_t)rfx);
 }
 
+// Two steps of one group at once with Blackwell's packed FP32 ops (each
+// half is an IEEE round-to-nearest operation, so both results are bitwise
+// those of depth_fx); the approximate reciprocals and square roots and the
+// conversions stay scalar.
+struct f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_pack(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 x, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_rcp(f2 x) {
+  float a, b;
+  f2_unpack(x, a, b);
+  return f2_pack(rcp_approx(a), rcp_approx(b));
+}
+__device__ __forceinline__ f2 f2_sqrt(f2 x) {
+  float a, b;
+  f2_unpack(x, a, b);
+  return f2_pack(sqrt_approx(a), sqrt_approx(b));
+}
+__device__ __forceinline__ f2 f2_splat(float a) { return f2_pack(a, a); }
+
+// depth_fx of steps s0 and s1 of group g, step for step the same operations
+__device__ __forceinline__ void depth_fx2(const GroupC &g, const StepC &s0, const StepC &s1,
+                                          const Consts &c, int32_t &d0, int32_t &d1) {
+  const f2 z = f2_pack(s0.zf, s1.zf);
+  f2 inv = f2_splat(g.invD);
+  f2 a = f2_mul(f2_splat(c.y0), z);
+  if (c.has_eta) {
+    const f2 eta = f2_pack(s0.eta, s1.eta);
+    inv = f2_rcp(f2_sub(f2_splat(g.D), eta));
+    a = f2_fma(eta, f2_add(f2_sub(z, f2_splat(g.Z)), f2_splat(g.Q0f)), a);
+  }
+  const f2 tap = f2_fma(a, inv, f2_add(z, f2_splat(g.Q0f)));
+  const f2 u = f2_sub(f2_splat(g.Z), tap);
+  const f2 L = f2_sqrt(f2_fma(u, u, f2_splat(g.Y2)));
+  const f2 num = f2_mul(tap, f2_sub(tap, f2_splat(__fadd_rn(g.Z, g.Z))));
+  const f2 dL = f2_mul(num, f2_rcp(f2_add(L, f2_splat(g.L0))));
+  const f2 rem = f2_mul(f2_fma(f2_splat(c.sR), dL, a), inv);
+  const f2 rs = f2_mul(rem, f2_splat(c.scale));
+  float r0, r1;
+  f2_unpack(rs, r0, r1);
+  d0 = (int32_t)((uint32_t)s0.zfx + (uint32_t)g.Q0fx + (uint32_t)__float2int_rn(r0));
+  d1 = (int32_t)((uint32_t)s1.zfx + (uint32_t)g.Q0fx + (uint32_t)__float2int_rn(r1));
+}
+
 // FP64 depth position of (group, step) relative to the plan origin.
 __device__ __forceinline__ double depth_f64(const GroupD &g, const StepD &s, const Consts &c) {
   const double z = s.z, Dm = g.D - s.eta;
@@ -155,6 +247,7 @@ __device__ __forceinline__ double depth_f64(const GroupD &g, const StepD &s, con
 
 struct GeoFx {
   using pos_t = int32_t;
+  static constexpr int kPixelsMinBlocks = 3;  // three 512-thread CTAs per SM
   using step_t = StepC;
   using group_t = GroupC;
   static __device__ __forceinline__ const StepC *steps(const Consts &c) { return c.stp; }
@@ -164,6 +257,11 @@ struct GeoFx {
   static __device__ __forceinline__ pos_t depth(const GroupC &g, const StepC &s,
                                                 const Consts &c) {
     return depth_fx(g, s, c);
+  }
+  static __device__ __forceinline__ void depth2(const GroupC &g, const StepC &s0,
+                                                const StepC &s1, const Consts &c, pos_t &d0,
+                                                pos_t &d1) {
+    depth_fx2(g, s0, s1, c, d0, d1);
   }
   static __device__ __forceinline__ pos_t edge(const Consts &c, int j) { return c.efx[j]; }
   // 1 / (b - a) for a < b (approximate reciprocal; same value in both kernels)
@@ -181,6 +279,7 @@ struct GeoFx {
 
 struct GeoF64 {
   using pos_t = double;
+  static constexpr int kPixelsMinBlocks = 1;  // the FP64 walk state needs more registers
   using step_t = StepD;
   using group_t = GroupD;
   static __device__ __forceinline__ const StepD *steps(const Consts &c) { return c.stp64; }
@@ -190,6 +289,12 @@ struct GeoF64 {
   static __device__ __forceinline__ pos_t depth(const GroupD &g, const StepD &s,
                                                 const Consts &c) {
     return depth_f64(g, s, c);
+  }
+  static __device__ __forceinline__ void depth2(const GroupD &g, const StepD &s0,
+                                                const StepD &s1, const Consts &c, pos_t &d0,
+                                                pos_t &d1) {
+    d0 = depth_f64(g, s0, c);
+    d1 = depth_f64(g, s1, c);
   }
   static __device__ __forceinline__ pos_t edge(const Consts &c, int j) { return c.e64[j]; }
   static __device__ __forceinline__ double inv_len(pos_t a, pos_t b) { return 1.0 / (b - a); }
@@ -542,9 +647,9 @@ __global__ void __launch_bounds__(512, 1) batch_rows_kernel(const BatchScan *__r
 
 // ------------------------------------------------------- pixels kernel ---
 // General geometry: every pixel has its own depth sequence.  A CTA owns one
-// row x tile_cols pixels x all steps; its warps are (slab, share) pairs: a
-// slab is 32 adjacent pixels (lane = pixel), and the bin_groups shares of a
-// slab split its bins.
+// row x tile_cols pixels x all steps; its threads are (pixel, slab, share):
+// a slab is 32 adjacent pixels (16 or 8 for narrower tiles), one per lane,
+// and the bin_groups shares of a slab split its bins.
 //  1. All threads evaluate the tile's K x tile_cols depth positions into
 //     shared memory (thread (pixel, share) takes steps share, share + G, ...)
 //     while the TMA copies the image tile.
@@ -560,21 +665,21 @@ __global__ void __launch_bounds__(512, 1) batch_rows_kernel(const BatchScan *__r
 // Shared-memory layout: [0, 128) mbarrier and the slab spans, then the image
 // tile [Kpad][tile_cols] uint16, the depth positions [K][tile_cols], the bin
 // edges [B + 1].
+// minimum / maximum over aligned groups of `width` lanes (a power of two
+// <= 32); every lane of the warp takes part
 template <class T>
-__device__ __forceinline__ T warp_min(T v) {
-#pragma unroll
-  for (int m = 16; m > 0; m >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, m));
+__device__ __forceinline__ T group_min(T v, int width) {
+  for (int m = width >> 1; m > 0; m >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, m));
   return v;
 }
 template <class T>
-__device__ __forceinline__ T warp_max(T v) {
-#pragma unroll
-  for (int m = 16; m > 0; m >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, m));
+__device__ __forceinline__ T group_max(T v, int width) {
+  for (int m = width >> 1; m > 0; m >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, m));
   return v;
 }
 
 template <class Geo, class OutT, bool kTma>
-__global__ void __launch_bounds__(1024) pixels_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks) pixels_kernel(const __grid_constant__ CUtensorMap tmap,
                                                          const uint16_t *__restrict__ img,
                                                          OutT *__restrict__ out, const Consts c,
                                                          const Tuning t) {
@@ -590,9 +695,12 @@ __global__ void __launch_bounds__(1024) pixels_kernel(const __grid_constant__ CU
                                            align16((size_t)K * TC * sizeof(pos_t)));
   const int row = blockIdx.y, c0 = blockIdx.x * TC;
   const int tid = threadIdx.x, NT = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nslab = TC >> 5;
-  const int slab = warp % nslab, share = warp / nslab;
-  const int lc = slab * 32 + lane;
+  // slabs of SW adjacent pixels (32, or the whole tile when it is narrower);
+  // thread = (pixel of its slab, slab, share)
+  const int SW = min(TC, 32), nslab = TC / SW, swl = __ffs(SW) - 1;  // SW: 8, 16 or 32
+  const int sl = tid & (SW - 1), grp = tid >> swl;
+  const int slab = grp % nslab, share = grp / nslab;
+  const int lc = slab * SW + sl;
   const int ncols = min(TC, c.W - c0);
   const bool valid = lc < ncols;
 
@@ -603,14 +711,20 @@ __global__ void __launch_bounds__(1024) pixels_kernel(const __grid_constant__ CU
   if (valid) {
     const auto g = Geo::group(c, row * c.W + c0 + lc);
     const auto *gsteps = Geo::steps(c);
-    for (int k = share; k < K; k += G) spos[k * TC + lc] = Geo::depth(g, gsteps[k], c);
+    for (int k = share; k < K; k += 2 * G) {  // steps k and k + G together
+      const int k2 = min(k + G, K - 1);
+      pos_t d0, d1;
+      Geo::depth2(g, gsteps[k], gsteps[k2], c, d0, d1);
+      spos[k * TC + lc] = d0;
+      if (k + G < K) spos[(k + G) * TC + lc] = d1;
+    }
   }
   for (int j = tid; j <= B; j += NT) sedge[j] = Geo::edge(c, j);
   __syncthreads();  // also makes the mbarrier initialisation visible
   auto pos = [&](int k) { return spos[k * TC + lc]; };
-  if (share == 0) {
-    const pos_t lo_d = warp_min(valid ? pos(0) : sedge[B]);
-    const pos_t hi_d = warp_max(valid ? pos(K - 1) : sedge[0]);
+  if (tid < max(TC, 32)) {  // whole warps holding the shares 0 of all slabs
+    const pos_t lo_d = group_min(valid ? pos(0) : sedge[B], SW);
+    const pos_t hi_d = group_max(valid ? pos(K - 1) : sedge[0], SW);
     int lo = 0, hi = B;
     while (lo < hi) {  // first j with e_{j+1} > min d_0
       const int mid = (lo + hi) >> 1;
@@ -622,36 +736,51 @@ __global__ void __launch_bounds__(1024) pixels_kernel(const __grid_constant__ CU
       const int mid = (lo + hi) >> 1;
       if (sedge[mid] < hi_d) lo = mid + 1; else hi = mid;
     }
-    if (lane == 0) span[slab] = make_int2(jlo, lo);
+    if (share == 0 && sl == 0) span[slab] = make_int2(jlo, lo);
   }
   __syncthreads();
   if constexpr (kTma) {
     if (!mbar_wait_bounded(bar, 0, c.err)) return;
   }
-  if (!valid) return;
   const int2 sp = span[slab];
   const float sign = c.out_sign, zero = __fmul_rn(sign, 0.f);
   const size_t plane = (size_t)c.H * c.W;
   const bool acc = c.accumulate != 0;
-  OutT *const o0 = out + (size_t)row * c.W + c0 + lc;
-  // this share's part of the bins outside the span
+  // the bins outside the span are zero: a full slab whose rows start on 16
+  // bytes stores them with 16-byte stores, the SW pixels of a bin being
+  // kVec stores, spread over all the slab's threads
   if (!acc) {
+    constexpr int kPer = 16 / sizeof(OutT);
+    const int kVec = SW / kPer, kvl = __ffs(kVec) - 1;  // 16-byte stores per bin
     const int nz = B - (sp.y - sp.x);
-    const int ib = (int)((long long)nz * share / G), ie = (int)((long long)nz * (share + 1) / G);
-    OutT *o = o0 + (size_t)ib * plane;  // [ib, ie) below the span: bins ib..
-    for (int i = ib; i < min(ie, sp.x); ++i, o += plane) st_cs(o, zero);
-    const int ia = max(ib, sp.x);       // the rest above it: bins i - jlo + jhi
-    o = o0 + (size_t)(ia - sp.x + sp.y) * plane;
-    for (int i = ia; i < ie; ++i, o += plane) st_cs(o, zero);
+    OutT *const os = out + (size_t)row * c.W + c0 + slab * SW;
+    if (slab * SW + SW <= ncols && c.W % kPer == 0 && ((uintptr_t)out & 15) == 0) {
+      const uint4 zv = zero_bits<OutT>(zero);
+      for (int i = share * SW + sl; i < nz * kVec; i += G * SW) {
+        const int z = i >> kvl, part = i & (kVec - 1);
+        const int j = z < sp.x ? z : z - sp.x + sp.y;
+        st_cs_u4(os + (size_t)j * plane + part * kPer, zv);
+      }
+    } else if (valid) {
+      for (int z = share; z < nz; z += G) {
+        const int j = z < sp.x ? z : z - sp.x + sp.y;
+        st_cs(os + (size_t)j * plane + sl, zero);
+      }
+    }
   }
+  if (!valid) return;
+  OutT *const o0 = out + (size_t)row * c.W + c0 + lc;
   // this share's part of the span
   const int nd = sp.y - sp.x;
   const int jb = sp.x + (int)((long long)nd * share / G);
   const int je = sp.x + (int)((long long)nd * (share + 1) / G);
   if (jb >= je) return;
   const pos_t tfirst = pos(0), tlast = pos(K - 1);
+  // image of step k at ip[k * istep] (steps stored in reverse for a reversed plan)
   const bool rev = c.reverse != 0;
-  auto spx = [&](int k) { return biased(simg[(size_t)(rev ? K - 1 - k : k) * TC + lc]); };
+  const uint16_t *ip = simg + (rev ? (K - 1) * TC : 0) + lc;
+  const int istep = rev ? -TC : TC;
+  auto spx = [&](int k) { return biased(ip[k * istep]); };
   // k = last step below e_jb, clamped to an interval
   pos_t e0 = sedge[jb];
   int lo = 0, hi = K;

@@ -435,23 +435,23 @@ static dr_status plan_one(const dr_geometry *g, const double *wires, int32_t K,
     t.bin_groups = bg;
     p->threads = lanes * bg;
   } else {
-    // per-pixel kernel: tile_cols pixels (slabs of 32) x bin_groups shares
+    // per-pixel kernel: tile_cols pixels (slabs of up to 32) x bin_groups shares
     t.ppt = 1;
     int tc = opt.tile_cols == 0 ? 32 : opt.tile_cols;
-    if (tc % 32 != 0 || tc > 256) {
+    if (!(tc == 8 || tc == 16 || (tc % 32 == 0 && tc <= 256))) {
       delete p;
-      set_error("dr_plan: per-pixel tile_cols must be a multiple of 32 in [32, 256]");
+      set_error("dr_plan: per-pixel tile_cols must be 8, 16 or a multiple of 32 up to 256");
       return DR_ERR_INVALID_ARG;
     }
     t.tile_cols = tc;
     int bg = opt.bin_groups;
     if (bg == 0) {
-      bg = std::max(1, 1024 / tc);
+      bg = std::max(1, 512 / tc);
       while (bg > 1 && B / bg < 16) bg /= 2;
     }
-    if (bg < 1 || tc * bg > 1024) {
+    if (bg < 1 || tc * bg > 512) {
       delete p;
-      set_error("dr_plan: per-pixel tile_cols x bin_groups must be at most 1024");
+      set_error("dr_plan: per-pixel tile_cols x bin_groups must be at most 512");
       return DR_ERR_INVALID_ARG;
     }
     t.bin_groups = bg;

@@ -97,6 +97,33 @@ def test_rotated_detector_per_pixel_depths():
     assert_parity(out.cpu().numpy(), ref_of(sc), sc.images)
 
 
+@pytest.fixture(scope="module", params=[280, 283])
+def rotated_ragged(request):
+    """Rotated detector whose width leaves a partial last tile for every tile
+    width: 280 columns (TMA staging, 16-byte zero stores) and 283 (plain
+    loads, scalar zero stores)."""
+    sc = synth.spot_scan(6, 3, request.param, 37, 10, -60.0, 60.0, 0.7, rotate_deg=9.0,
+                         tilt_deg=3.0, depth_range=(-0.03, 0.03))
+    plan, out = run(sc)
+    assert plan.info()["kernel"] == "pixels"
+    assert_parity(out.cpu().numpy(), ref_of(sc), sc.images)
+    return sc, out
+
+
+@pytest.mark.parametrize("tc,bg", [(32, 16), (16, 32), (16, 16), (8, 64), (32, 8), (64, 8),
+                                   (8, 1), (96, 4), (256, 2)])
+def test_per_pixel_launch_shapes_agree(rotated_ragged, tc, bg):
+    """Every tile width / share count gives bitwise the same bins, for full
+    and partial slabs, vector and scalar zero stores."""
+    sc, ref = rotated_ragged
+    plan = dr.Plan(sc.geom, sc.wires, sc.edges, tile_cols=tc, bin_groups=bg)
+    info = plan.info()
+    assert (info["kernel"], info["tile_cols"], info["bin_groups"]) == ("pixels", tc, bg)
+    out = plan.reconstruct(to_dev(sc.images))
+    torch.cuda.synchronize()
+    assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
+
+
 @pytest.mark.parametrize("edge", ["leading", "trailing"])
 def test_edges_and_reversed_travel(edge):
     sc = synth.tiny_scan(5, rows=16, cols=40, K=25)
