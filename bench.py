@@ -723,6 +723,8 @@ def main():
     ap.add_argument("--rotate", type=float, default=0.0,
                     help="rotate the detector in its plane (degrees): per-pixel depths")
     ap.add_argument("--tilt", type=float, default=0.0, help="tilt the detector about x (degrees)")
+    ap.add_argument("--intervals", action="store_true",
+                    help="use the interval kernel (depths in any order) on the same scan")
     ap.add_argument("--rows", type=int, default=2048,
                     help="reconstruct only the first ROWS detector rows (small profiling case)")
     args = ap.parse_args()
@@ -789,7 +791,10 @@ def main():
 
     out = torch.empty((spec.B, spec.geom["rows"], spec.geom["cols"]), dtype=torch.float32,
                       device=dev)
-    if args.tile_cols:
+    if args.intervals:
+        plan = dr.Plan(spec.geom, spec.wires, spec.edges, force_intervals=True)
+        tuned = None
+    elif args.tile_cols:
         plan = dr.Plan(spec.geom, spec.wires, spec.edges, tile_cols=args.tile_cols,
                        bin_groups=args.bin_groups)
         tuned = None
@@ -840,8 +845,9 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": peak_kind,
-                "kernel": ("rows_kernel<GeoFx,float,tma,4>" if info["kernel"] == "rows"
-                           else "pixels_kernel<GeoFx,float,tma>"),
+                "kernel": {"rows": "rows_kernel<GeoFx,float,tma,4>",
+                           "pixels": "pixels_kernel<GeoFx,float,tma>",
+                           "intervals": "intervals_kernel<GeoFx,float,tma>"}[info["kernel"]],
                 "algorithmic_bytes_per_launch": alg_bytes}
 
     # end to end through the public API with host buffers: the streamed form
@@ -912,7 +918,9 @@ def main():
             "config": {"workload": (WORKLOAD if args.rows == 2048 else
                                     WORKLOAD + f" (first {args.rows} rows only)")
                        + (f"; detector rotated {args.rotate} deg, tilted {args.tilt} deg"
-                          if args.rotate or args.tilt else ""), "pixels": P, "wire_steps": spec.K,
+                          if args.rotate or args.tilt else "")
+                       + ("; interval kernel (depths in any order) forced"
+                          if args.intervals else ""), "pixels": P, "wire_steps": spec.K,
                        "bins": spec.B, "parallelism": f"replicas x{world}",
                        "l2": f"input ({2 * units_per_step / 1e9:.2f} GB) and output "
                              f"({4 * P * spec.B / 1e9:.1f} GB) larger than L2; no flush",

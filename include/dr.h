@@ -44,8 +44,9 @@ typedef enum {
   DR_ERR_INVALID_ARG = 1,   /* null pointer, bad size, unsorted bin edges */
   DR_ERR_GEOMETRY = 2,      /* beam along the wire, pixel inside the wire, wire
                                not between beam and detector, no travel */
-  DR_ERR_NONMONOTONIC = 3,  /* depth sequence of some pixel not strictly
-                               monotone in the step index */
+  DR_ERR_NONMONOTONIC = 3,  /* depth sequence not strictly monotone where an
+                               entry point needs it (the no-allocation rows
+                               entry); dr_plan itself takes any order */
   DR_ERR_OOM = 4,           /* device or host allocation failed */
   DR_ERR_BUDGET = 5,        /* request does not fit the memory budget */
   DR_ERR_CUDA = 6,          /* a CUDA runtime call failed */
@@ -56,7 +57,7 @@ typedef enum {
 enum { DR_EDGE_LEADING = 0, DR_EDGE_TRAILING = 1, DR_EDGE_BOTH = 2 };
 enum { DR_OUT_F32 = 0, DR_OUT_BF16 = 1 };
 enum { DR_GEOM_FP32 = 0, DR_GEOM_FP64 = 1 };
-enum { DR_KERNEL_ROWS = 0, DR_KERNEL_PIXELS = 1 };
+enum { DR_KERNEL_ROWS = 0, DR_KERNEL_PIXELS = 1, DR_KERNEL_INTERVALS = 2 };
 
 /* Scan geometry.  Pixel (r, c) has its centre at
  * det_origin + r*row_step + c*col_step.  The wire is an infinite cylinder of
@@ -90,7 +91,9 @@ typedef struct {
   int32_t bin_groups;       /* warps-groups splitting the bins; 0 = tuned */
   int32_t force_pixels;     /* 1: use the per-pixel kernel even when all
                                pixels of a row share their depths */
-  int32_t reserved[3];
+  int32_t force_intervals;  /* 1: use the interval kernel (depths in any
+                               order) even when every sequence is monotone */
+  int32_t reserved[2];
 } dr_plan_options;
 
 typedef struct dr_plan dr_plan_t;
@@ -98,8 +101,12 @@ typedef struct dr_plan dr_plan_t;
 /* What a plan decided (for reports and tests). */
 typedef struct {
   int32_t rows, cols, K, B;
-  int32_t kernel;           /* DR_KERNEL_ROWS or DR_KERNEL_PIXELS */
-  int32_t tile_cols, pixels_per_thread, bin_groups, threads;
+  int32_t kernel;           /* DR_KERNEL_ROWS, DR_KERNEL_PIXELS or
+                               DR_KERNEL_INTERVALS */
+  int32_t tile_cols, pixels_per_thread;
+  int32_t bin_groups;       /* thread groups splitting the bins; for the
+                               interval kernel, bins per shared-memory window */
+  int32_t threads;
   int32_t smem_bytes, tma_chunk, tma_chunks;
   int32_t out_dtype, geom_precision, edge, reversed;
   int32_t fixed_shift;      /* depth positions in units of 2^-fixed_shift mm
@@ -116,11 +123,17 @@ typedef struct {
 } dr_plan_info;
 
 /* Build a plan: validate the geometry, compute the per-pixel (or per-row,
- * when all pixels of a row share their depths) constants in FP64, check that
+ * when all pixels of a row share their depths) constants in FP64, upload them
+ * and pick the kernel and tile shape.  The apportioning of Sec. III spreads
+ * each difference over the interval between two consecutive depths.  When
  * every depth sequence is strictly monotone within each run of the wire path
- * (the path may turn back along the beam; two consecutive centres at the same
- * position along the beam are rejected), upload the constants and pick the
- * kernel and tile shape.
+ * (the path may turn back along the beam) the plan uses the running-sum
+ * kernels (rows or per-pixel); otherwise (a wire that also moves across the
+ * beam, two centres at the same position along the beam) it uses the
+ * interval kernel, which adds each interval by itself in any order; a
+ * zero-length interval puts its difference in the bin that holds it.  The
+ * wire must travel along the beam between its first and last centre
+ * (DR_ERR_GEOMETRY otherwise).
  *   wire_centres  host [K][3] FP64, K >= 2
  *   bin_edges     host [B+1] FP64 strictly increasing (depth, mm), B >= 1
  * rows or cols may be 0 (an empty ROI: dr_reconstruct then does nothing).

@@ -13,7 +13,9 @@
 
 struct dr_plan {
   int rows, cols, K, B, edge;
-  int kernel;              // DR_KERNEL_ROWS / DR_KERNEL_PIXELS
+  int kernel;              // DR_KERNEL_ROWS / DR_KERNEL_PIXELS / DR_KERNEL_INTERVALS
+  int pixel_groups;        // 1: geometry constants per pixel, 0: per row
+  int window;              // interval kernel: bins per shared-memory window
   int out_dtype, geom_prec;
   int shift;
   double nb;               // |projected beam direction|: depth = t / nb
@@ -55,6 +57,16 @@ constexpr int kSmemPerCtaMax = 227 * 1024;   // opt-in maximum per CTA
 // Shared-memory bytes of one rows / pixels tile (layouts in dr_device.cuh).
 int rows_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64);
 int pixels_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64);
+// Interval kernel: pixels per CTA (one warp each), and the shared-memory
+// bytes of one tile: mbarrier, image tile [Kpad][8] uint16, depths [K][8],
+// edges [B + 1], int64 accumulators [window][8] (dr_intervals.cuh).
+constexpr int kIntervalTile = 8;
+inline int intervals_smem(int K, int Kpad, int B, int window, bool f64) {
+  const size_t ps = f64 ? 8 : 4;
+  auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  return (int)(128 + a16((size_t)Kpad * kIntervalTile * 2) + a16((size_t)K * kIntervalTile * ps) +
+               a16((size_t)(B + 1) * ps) + (size_t)window * kIntervalTile * 8);
+}
 // TMA chunking of K steps for a tile width (128-byte aligned destinations).
 void choose_chunks(int K, int tile_cols, int *kc, int *nchunks);
 // Raise a kernel's dynamic shared-memory limit (once per device).

@@ -1,0 +1,151 @@
+// Interval kernel: apportioning for depth sequences in any order.
+//
+// The method spreads each image difference dI_k = I_k - I_{k+1} over the depth
+// interval swept between steps k and k+1 in proportion to its overlap with
+// each bin (Sec. III).  The rows and per-pixel kernels evaluate that sum as a
+// running sum F, which needs the depths of a pixel to increase with k.  When
+// they do not (a wire that also moves across the beam, repeated positions),
+// the plan falls back to this kernel, which adds every interval by itself:
+//
+//   out_j = sum_k dI_k * (phi_k(e_{j+1}) - phi_k(e_j)),
+//   phi_k(x) = clamp((x - lo_k) / (hi_k - lo_k), 0, 1),
+//   lo_k = min(d_k, d_{k+1}), hi_k = max(d_k, d_{k+1}),
+//
+// and an interval of zero length puts its whole dI_k into the bin
+// [e_j, e_{j+1}) that holds it.  Mass outside [e_0, e_B] is dropped.
+//
+// A CTA owns one row x 8 adjacent pixels x all K steps (image tile staged by
+// TMA as in the other kernels, depths of the 8 pixels in shared memory), one
+// warp per pixel.  The bins go through shared-memory windows of `window`
+// int64 accumulators per pixel; the lanes of a warp take the pixel's
+// intervals in turn and add dI * phi(e) on the fixed-point grid 2^-30
+// (Phi(e_{j+1}) - Phi(e_j), so the parts of one interval add up to dI
+// exactly) with shared-memory atomics.  Integer sums do not depend on the
+// order of the atomics, so the result is deterministic.  The window is then
+// written out, 8 pixels of one bin being one 32-byte sector.
+#pragma once
+
+#include "dr_device.cuh"
+#include "dr_internal.h"
+
+namespace dr {
+
+constexpr double kIvScale = 1073741824.0;  // 2^30: fixed-point grid of the sums
+
+// Phi(e) = round(dI * phi(e) * 2^30), phi(e) = clamp((e - lo) / (hi - lo), 0, 1)
+__device__ __forceinline__ long long iv_phi(int32_t e, int32_t lo, float inv_len, float dI) {
+  const float f = fminf(fmaxf(__fmul_rn((float)((long long)e - lo), inv_len), 0.f), 1.f);
+  return __float2ll_rn(__fmul_rn(__fmul_rn(dI, f), (float)kIvScale));
+}
+__device__ __forceinline__ long long iv_phi(double e, double lo, double inv_len, float dI) {
+  const double f = fmin(fmax((e - lo) * inv_len, 0.0), 1.0);
+  return __double2ll_rn((double)dI * f * kIvScale);
+}
+__device__ __forceinline__ float iv_inv_len(int32_t lo, int32_t hi) {
+  return __frcp_rn((float)((long long)hi - lo));
+}
+__device__ __forceinline__ double iv_inv_len(double lo, double hi) { return 1.0 / (hi - lo); }
+
+template <class Geo, class OutT, bool kTma>
+__global__ void __launch_bounds__(256) intervals_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                        const uint16_t *__restrict__ img,
+                                                        OutT *__restrict__ out, const Consts c,
+                                                        const Tuning t, int pixel_groups,
+                                                        int window) {
+  using pos_t = typename Geo::pos_t;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  uint16_t *simg = reinterpret_cast<uint16_t *>(smem + 128);
+  constexpr int TC = kIntervalTile;
+  const int K = c.K, B = c.B;
+  const int Kpad = t.kc * t.nchunks;
+  pos_t *spos = reinterpret_cast<pos_t *>(smem + 128 + align16((size_t)Kpad * TC * 2));
+  pos_t *sedge = reinterpret_cast<pos_t *>(reinterpret_cast<unsigned char *>(spos) +
+                                           align16((size_t)K * TC * sizeof(pos_t)));
+  unsigned long long *acc = reinterpret_cast<unsigned long long *>(
+      reinterpret_cast<unsigned char *>(sedge) + align16((size_t)(B + 1) * sizeof(pos_t)));
+  const int row = blockIdx.y, c0 = blockIdx.x * TC;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int ncols = min(TC, c.W - c0);
+
+  if constexpr (kTma) {
+    if (tid == 0) mbar_init(bar, 1);
+  }
+  stage_tile<kTma>(&tmap, img, simg, bar, c, t, row, c0);
+  {  // depths of the tile: thread -> pixel tid % 8, steps tid / 8, + NT / 8, ...
+    const int lc = tid % TC;
+    if (lc < ncols) {
+      const auto g = Geo::group(c, pixel_groups ? row * c.W + c0 + lc : row);
+      const auto *steps = Geo::steps(c);
+      for (int k = tid / TC; k < K; k += NT / TC) spos[k * TC + lc] = Geo::depth(g, steps[k], c);
+    }
+  }
+  for (int j = tid; j <= B; j += NT) sedge[j] = Geo::edge(c, j);
+  __syncthreads();  // also makes the mbarrier initialisation visible
+  if constexpr (kTma) {
+    const bool late = !mbar_wait_bounded(bar, 0, c.err);
+    if (__syncthreads_or(late)) return;
+  }
+
+  const int warp = tid >> 5, lane = tid & 31, nwarps = NT >> 5;
+  const bool rev = c.reverse != 0;
+  const float sign = c.out_sign;
+  const size_t plane = (size_t)c.H * c.W;
+  const bool acc_out = c.accumulate != 0;
+  // number of edges e_i <= x (0..B+1)
+  auto count_le = [&](pos_t x) {
+    int lo = 0, hi = B + 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sedge[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+  };
+
+  for (int wb0 = 0; wb0 < B; wb0 += window) {
+    const int wb1 = min(wb0 + window, B);
+    const int nwin = (wb1 - wb0) * TC;
+    for (int i = tid; i < nwin; i += NT) acc[i] = 0ull;
+    __syncthreads();
+    const pos_t ewlo = sedge[wb0], ewhi = sedge[wb1];
+    for (int lc = warp; lc < ncols; lc += nwarps) {
+      for (int m = lane; m < K - 1; m += 32) {
+        const int ia = rev ? K - 1 - m : m, ib = rev ? K - 2 - m : m + 1;
+        const int dI = (int)simg[ia * TC + lc] - (int)simg[ib * TC + lc];
+        if (dI == 0) continue;
+        const pos_t a = spos[m * TC + lc], b = spos[(m + 1) * TC + lc];
+        const pos_t lo = a < b ? a : b, hi = a < b ? b : a;
+        if (lo >= ewhi || hi < ewlo) continue;  // nothing in this window
+        const int u = count_le(lo);
+        if (!(hi > lo)) {  // zero length: the bin [e_j, e_{j+1}) holding lo
+          const int j = u - 1;
+          if (j >= wb0 && j < wb1)
+            atomicAdd(&acc[(j - wb0) * TC + lc],
+                      (unsigned long long)((long long)dI * (long long)kIvScale));
+          continue;
+        }
+        const auto inv = iv_inv_len(lo, hi);
+        const float dIf = (float)dI;
+        int j = max(u - 1, wb0);
+        long long p0 = iv_phi(sedge[j], lo, inv, dIf);
+        for (; j < wb1 && sedge[j] < hi; ++j) {
+          const long long p1 = iv_phi(sedge[j + 1], lo, inv, dIf);
+          if (p1 != p0) atomicAdd(&acc[(j - wb0) * TC + lc], (unsigned long long)(p1 - p0));
+          p0 = p1;
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < nwin; i += NT) {
+      const int jj = i / TC, lc = i - jj * TC;
+      if (lc >= ncols) continue;
+      OutT *o = out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + lc;
+      const float v =
+          __fmul_rn(sign, (float)((double)(long long)acc[i] * (1.0 / kIvScale)));
+      st_cs(o, acc_out ? __fadd_rn(out_load(o), v) : v);
+    }
+    __syncthreads();  // the window's accumulators are reused
+  }
+}
+
+}  // namespace dr

@@ -127,7 +127,7 @@ void choose_chunks(int K, int tile_cols, int *kc, int *nchunks) {
 // One monotone plan.  side != 0 fixes the tangent side s (the wire edge
 // chosen by the whole scan's travel), for the runs of a composite plan whose
 // own travel may point the other way.
-static dr_status plan_one(const dr_geometry *g, const double *wires, int32_t K,
+static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wires, int32_t K,
                           const double *edges, int32_t B, const dr_plan_options *opt_in,
                           int side, dr_plan_t **out) {
   if (out) *out = nullptr;
@@ -289,11 +289,13 @@ static dr_status plan_one(const dr_geometry *g, const double *wires, int32_t K,
       remmax = std::max(remmax, std::fabs(t - zp[k] - q.Q0));
       if (all_steps && k > 0) {
         double st = t - prev;
-        if (!(st > 0)) {
+        if (intervals) {  // any order: only the smallest nonzero step is kept
+          if (st != 0) minstep = std::min(minstep, std::fabs(st));
+        } else if (!(st > 0)) {
           *bad_k = k;
           return false;
         }
-        minstep = std::min(minstep, st);
+        else minstep = std::min(minstep, st);
       }
       prev = t;
     }
@@ -339,7 +341,8 @@ static dr_status plan_one(const dr_geometry *g, const double *wires, int32_t K,
     return DR_ERR_UNSUPPORTED;
   }
   const double scale = std::ldexp(1.0, shift);
-  if (P > 0 && minstep * scale < 64.0) {
+  if (minstep == 1e300) minstep = 0.0;  // interval kernel, no nonzero step seen
+  if (P > 0 && !intervals && minstep * scale < 64.0) {
     set_error("dr_plan: depth steps (%.3g mm) too small for the fixed-point grid", minstep);
     return DR_ERR_UNSUPPORTED;
   }
@@ -388,7 +391,8 @@ static dr_status plan_one(const dr_geometry *g, const double *wires, int32_t K,
   p->K = K;
   p->B = B;
   p->edge = g->edge;
-  p->kernel = rows_shared ? DR_KERNEL_ROWS : DR_KERNEL_PIXELS;
+  p->kernel = intervals ? DR_KERNEL_INTERVALS : rows_shared ? DR_KERNEL_ROWS : DR_KERNEL_PIXELS;
+  p->pixel_groups = rows_shared ? 0 : 1;
   p->out_dtype = opt.out_dtype;
   p->geom_prec = opt.geom_precision;
   p->shift = shift;
@@ -404,7 +408,19 @@ static dr_status plan_one(const dr_geometry *g, const double *wires, int32_t K,
     return rows_shared ? rows_smem_bytes(K, kc * n, B, tc, f64)
                        : pixels_smem_bytes(K, kc * n, B, tc, f64);
   };
-  if (rows_shared) {
+  if (intervals) {
+    // 8 pixels x all steps per CTA, one warp per pixel; bins in windows of
+    // int64 accumulators sized for two CTAs per SM (one if that is too small)
+    t.ppt = 1;
+    t.tile_cols = kIntervalTile;
+    t.bin_groups = 1;
+    p->threads = 256;
+    if (K > 65535) {
+      delete p;
+      set_error("dr_plan: the interval kernel takes at most 65535 steps");
+      return DR_ERR_UNSUPPORTED;
+    }
+  } else if (rows_shared) {
     t.ppt = (W % 4 == 0) ? 4 : 1;
     int tc = opt.tile_cols;
     if (tc == 0) {
@@ -463,7 +479,23 @@ static dr_status plan_one(const dr_geometry *g, const double *wires, int32_t K,
     set_error("dr_plan: no aligned TMA chunking for K=%d, tile_cols=%d", K, t.tile_cols);
     return DR_ERR_UNSUPPORTED;
   }
-  p->smem_bytes = smem_for(t.tile_cols);
+  if (intervals) {
+    const size_t fixed = (size_t)intervals_smem(K, t.kc * t.nchunks, B, 0, f64);
+    size_t budget = (size_t)(kSmemPerSm / 2 - 1024);
+    if (fixed + 32 * 64 > budget) budget = (size_t)kSmemPerCtaMax;
+    const long long win = fixed < budget ? (long long)((budget - fixed) / 64) : 0;
+    if (win < std::min(B, 32)) {
+      delete p;
+      set_error("dr_plan: %d steps x %d bins do not fit the interval kernel's shared memory", K,
+                B);
+      return DR_ERR_UNSUPPORTED;
+    }
+    p->window = (int)std::min<long long>(win, B);
+    t.bin_groups = p->window;
+    p->smem_bytes = intervals_smem(K, t.kc * t.nchunks, B, p->window, f64);
+  } else {
+    p->smem_bytes = smem_for(t.tile_cols);
+  }
   if (p->smem_bytes > kSmemPerCtaMax) {
     delete p;
     set_error("dr_plan: %d steps x %d columns do not fit in shared memory", K, t.tile_cols);
@@ -486,7 +518,8 @@ static dr_status plan_one(const dr_geometry *g, const double *wires, int32_t K,
   // above 1 GiB the tiles build their own)
   const int tab_stride = row_table_entries(B);
   const size_t tab_bytes = (size_t)H * tab_stride * 8;
-  const bool row_tables = rows_shared && H > 0 && W > 0 && tab_bytes <= (size_t(1) << 30);
+  const bool row_tables =
+      p->kernel == DR_KERNEL_ROWS && H > 0 && W > 0 && tab_bytes <= (size_t(1) << 30);
   size_t o_tab = row_tables ? take(tab_bytes) : 0;
   size_t total = align_up(off, 256);
   void *blk = nullptr;
@@ -559,54 +592,16 @@ static dr_status plan_one(const dr_geometry *g, const double *wires, int32_t K,
 // whole scan's wire edge, and the runs' outputs add up (the apportioning is a
 // sum over intervals).  DR_EDGE_BOTH is the mean of the leading- and
 // trailing-edge reconstructions.  Single-run, single-edge scans are one plan.
-extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t K,
-                             const double *edges, int32_t B, const dr_plan_options *opt,
-                             dr_plan_t **out) {
-  if (out) *out = nullptr;
-  if (!g || !wires || !edges || !out) {
-    set_error("dr_plan: null argument");
-    return DR_ERR_INVALID_ARG;
-  }
-  if (K < 2 || B < 1) {
-    set_error("dr_plan: need K >= 2, B >= 1 (K=%d B=%d)", K, B);
-    return DR_ERR_INVALID_ARG;
-  }
+// Depth sequences that are not monotone within a run (a wire that also moves
+// across the beam, two steps at the same position) take the interval kernel,
+// which adds every interval by itself and accepts any order.
+static dr_status plan_parts(bool intervals, const dr_geometry *g, const double *wires,
+                            int32_t K, const double *edges, int32_t B,
+                            const dr_plan_options *opt, const std::vector<int> &starts,
+                            double travel, dr_plan_t **out) {
   const bool both = g->edge == DR_EDGE_BOTH;
-  // projected wire position along the beam (the plan's e2 coordinate)
-  std::vector<int> starts{0};
-  double travel = 0.0;
-  {
-    V3 ax = v3(g->wire_axis), bd = v3(g->beam_dir), O = v3(g->beam_origin);
-    if (norm(ax) > 0 && norm(bd) > 0 && finite3(wires) && finite3(wires + 3 * (K - 1))) {
-      ax = (1.0 / norm(ax)) * ax;
-      bd = (1.0 / norm(bd)) * bd;
-      const V3 bp = bd - dot(bd, ax) * ax;
-      if (norm(bp) > 1e-9) {
-        const V3 e2 = (1.0 / norm(bp)) * bp;
-        travel = dot(v3(wires + 3 * (K - 1)) - v3(wires), e2);
-        int dir = 0;
-        for (int k = 0; k + 1 < K && travel != 0.0; ++k) {
-          if (!finite3(wires + 3 * k) || !finite3(wires + 3 * (k + 1))) break;
-          const double dz = dot(v3(wires + 3 * (k + 1)) - v3(wires + 3 * k), e2);
-          if (dz == 0.0) {
-            set_error("dr_plan: wire steps %d and %d at the same position along the beam", k,
-                      k + 1);
-            return DR_ERR_NONMONOTONIC;
-          }
-          const int d = dz > 0 ? 1 : -1;
-          if (dir != 0 && d != dir) starts.push_back(k);  // run turns at step k
-          dir = d;
-        }
-      }
-    }
-  }
-  // a single run (and a wire that does not travel: plan_one reports it)
-  if ((starts.size() == 1 || travel == 0.0) && !both)
-    return plan_one(g, wires, K, edges, B, opt, 0, out);
-  if (travel == 0.0) {
-    set_error("dr_plan: the wire ends where it started along the beam (no travel)");
-    return DR_ERR_GEOMETRY;
-  }
+  if (starts.size() == 1 && !both)
+    return plan_one(intervals, g, wires, K, edges, B, opt, 0, out);
   dr_plan_t *top = new (std::nothrow) dr_plan_t();
   if (!top) {
     set_error("dr_plan: host allocation failed");
@@ -621,7 +616,8 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t 
       const int k0 = starts[r];
       const int k1 = r + 1 < starts.size() ? starts[r + 1] : K - 1;  // inclusive
       dr_plan_t *part = nullptr;
-      dr_status st = plan_one(&ge, wires + 3 * k0, k1 - k0 + 1, edges, B, opt, side, &part);
+      dr_status st =
+          plan_one(intervals, &ge, wires + 3 * k0, k1 - k0 + 1, edges, B, opt, side, &part);
       if (st != DR_OK) {
         dr_plan_destroy(top);
         return st;
@@ -639,6 +635,8 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t 
   top->B = B;
   top->edge = g->edge;
   top->kernel = f->kernel;
+  top->pixel_groups = f->pixel_groups;
+  top->window = f->window;
   top->out_dtype = f->out_dtype;
   top->geom_prec = f->geom_prec;
   top->shift = f->shift;
@@ -658,6 +656,62 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t 
   top->smem_bytes = f->smem_bytes;
   *out = top;
   return DR_OK;
+}
+
+extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t K,
+                             const double *edges, int32_t B, const dr_plan_options *opt,
+                             dr_plan_t **out) {
+  if (out) *out = nullptr;
+  if (!g || !wires || !edges || !out) {
+    set_error("dr_plan: null argument");
+    return DR_ERR_INVALID_ARG;
+  }
+  if (K < 2 || B < 1) {
+    set_error("dr_plan: need K >= 2, B >= 1 (K=%d B=%d)", K, B);
+    return DR_ERR_INVALID_ARG;
+  }
+  const bool force_iv = opt && opt->force_intervals;
+  // projected wire position along the beam (the plan's e2 coordinate):
+  // monotone runs, or a repeated position (interval kernel)
+  std::vector<int> starts{0};
+  double travel = 0.0;
+  bool repeated = false;
+  {
+    V3 ax = v3(g->wire_axis), bd = v3(g->beam_dir), O = v3(g->beam_origin);
+    if (norm(ax) > 0 && norm(bd) > 0 && finite3(wires) && finite3(wires + 3 * (K - 1))) {
+      ax = (1.0 / norm(ax)) * ax;
+      bd = (1.0 / norm(bd)) * bd;
+      const V3 bp = bd - dot(bd, ax) * ax;
+      if (norm(bp) > 1e-9) {
+        const V3 e2 = (1.0 / norm(bp)) * bp;
+        travel = dot(v3(wires + 3 * (K - 1)) - v3(wires), e2);
+        int dir = 0;
+        for (int k = 0; k + 1 < K && travel != 0.0; ++k) {
+          if (!finite3(wires + 3 * k) || !finite3(wires + 3 * (k + 1))) break;
+          const double dz = dot(v3(wires + 3 * (k + 1)) - v3(wires + 3 * k), e2);
+          if (dz == 0.0) {
+            repeated = true;
+            break;
+          }
+          const int d = dz > 0 ? 1 : -1;
+          if (dir != 0 && d != dir) starts.push_back(k);  // run turns at step k
+          dir = d;
+        }
+      }
+    }
+  }
+  if (travel == 0.0) {  // plan_one reports the geometry (or no travel)
+    if (g->edge != DR_EDGE_BOTH) return plan_one(force_iv, g, wires, K, edges, B, opt, 0, out);
+    set_error("dr_plan: the wire ends where it started along the beam (no travel)");
+    return DR_ERR_GEOMETRY;
+  }
+  const std::vector<int> one{0};
+  if (force_iv || repeated)
+    return plan_parts(true, g, wires, K, edges, B, opt, one, travel, out);
+  dr_status st = plan_parts(false, g, wires, K, edges, B, opt, starts, travel, out);
+  if (st == DR_ERR_NONMONOTONIC)  // depth runs against its wire run somewhere
+    st = plan_parts(true, g, wires, K, edges, B, opt, one, travel, out);
+  return st;
 }
 
 extern "C" void dr_plan_destroy(dr_plan_t *p) {

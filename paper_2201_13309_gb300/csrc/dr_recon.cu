@@ -13,6 +13,8 @@
 //                 positions go to shared memory once, then the warps split
 //                 the bins evenly and each lane walks its pixel's steps and
 //                 bins together (merge-walk).
+//  intervals_kernel  depths in any order (dr_intervals.cuh): every interval
+//                 is added by itself into shared-memory accumulators.
 //
 // F is the running sum of the differences, linearly interpolated in depth
 // between step depths, so F_{j+1} - F_j equals the sum over intervals of
@@ -31,6 +33,7 @@
 
 #include "dr_device.cuh"
 #include "dr_internal.h"
+#include "dr_intervals.cuh"
 
 namespace dr {
 
@@ -103,9 +106,24 @@ dr_status launch_pixels(const dr_plan_t *p, const CUtensorMap &tm, const uint16_
   return DR_OK;
 }
 
+template <class Geo, class OutT, bool kTma>
+dr_status launch_intervals(const dr_plan_t *p, const CUtensorMap &tm, const uint16_t *img,
+                           void *out, cudaStream_t st) {
+  auto fn = intervals_kernel<Geo, OutT, kTma>;
+  dr_status s = allow_smem((const void *)fn);
+  if (s != DR_OK) return s;
+  dim3 grid((p->cols + kIntervalTile - 1) / kIntervalTile, p->rows);
+  fn<<<grid, p->threads, p->smem_bytes, st>>>(tm, img, (OutT *)out, p->c, p->tune,
+                                              p->pixel_groups, p->window);
+  return DR_OK;
+}
+
 template <class Geo, class OutT>
 dr_status dispatch_out(const dr_plan_t *p, bool tma, const CUtensorMap &tm, const uint16_t *img,
                        void *out, cudaStream_t st) {
+  if (p->kernel == DR_KERNEL_INTERVALS)
+    return tma ? launch_intervals<Geo, OutT, true>(p, tm, img, out, st)
+               : launch_intervals<Geo, OutT, false>(p, tm, img, out, st);
   if (p->kernel == DR_KERNEL_ROWS) {
     if (p->tune.ppt == 4)
       return tma ? launch_rows<Geo, OutT, true, 4>(p, tm, img, out, st)
@@ -154,6 +172,10 @@ dr_status preload_kernels() {
       (const void *)pixels_kernel<GeoFx, float, false>,
       (const void *)pixels_kernel<GeoFx, __nv_bfloat16, true>,
       (const void *)pixels_kernel<GeoFx, __nv_bfloat16, false>,
+      (const void *)intervals_kernel<GeoFx, float, true>,
+      (const void *)intervals_kernel<GeoFx, float, false>,
+      (const void *)intervals_kernel<GeoFx, __nv_bfloat16, true>,
+      (const void *)intervals_kernel<GeoFx, __nv_bfloat16, false>,
   };
   for (const void *f : fns) {
     dr_status s = allow_smem(f);
@@ -305,10 +327,12 @@ extern "C" dr_status dr_plan_depths(const dr_plan_t *p, int32_t r0, int32_t nrow
   }
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 32) blocks = 152 * 32;
+  // the depth kernel picks the group layout from a kernel kind
+  const int layout = p->pixel_groups ? DR_KERNEL_PIXELS : DR_KERNEL_ROWS;
   if (p->geom_prec == DR_GEOM_FP64)
-    depths_kernel<GeoF64><<<blocks, 256, 0, (cudaStream_t)stream>>>(p->c, p->kernel, r0, nrows, d);
+    depths_kernel<GeoF64><<<blocks, 256, 0, (cudaStream_t)stream>>>(p->c, layout, r0, nrows, d);
   else
-    depths_kernel<GeoFx><<<blocks, 256, 0, (cudaStream_t)stream>>>(p->c, p->kernel, r0, nrows, d);
+    depths_kernel<GeoFx><<<blocks, 256, 0, (cudaStream_t)stream>>>(p->c, layout, r0, nrows, d);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail("dr_plan_depths", e);
   return DR_OK;
@@ -509,7 +533,7 @@ extern "C" dr_status dr_reconstruct_streamed(const dr_plan_t *p, const uint16_t 
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->comp, ss->start, 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->down, ss->start, 0);
   if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: fork", e);
-  const int groups_per_row = p->kernel == DR_KERNEL_ROWS ? 1 : W;
+  const int groups_per_row = p->pixel_groups ? W : 1;
   const int nslab = (H + slab_rows - 1) / slab_rows;
   for (int i = 0; i < nslab; ++i) {
     const int b = i % nbuf, r0 = i * slab_rows, n = std::min(slab_rows, H - r0);
@@ -760,8 +784,9 @@ extern "C" dr_status dr_reconstruct_selected(const dr_plan_t *p, const uint16_t 
     set_error("dr_reconstruct_selected: bad arguments");
     return DR_ERR_INVALID_ARG;
   }
-  if (!p->parts.empty()) {
-    set_error("dr_reconstruct_selected: not available for plans of several runs or both edges");
+  if (!p->parts.empty() || p->kernel == DR_KERNEL_INTERVALS) {
+    set_error("dr_reconstruct_selected: not available for plans of several runs or both edges"
+              " or for the interval kernel");
     return DR_ERR_UNSUPPORTED;
   }
   if (n == 0 || (size_t)p->rows * p->cols == 0) return DR_OK;

@@ -23,7 +23,7 @@ STATUS = {0: "DR_OK", 1: "DR_ERR_INVALID_ARG", 2: "DR_ERR_GEOMETRY",
 EDGES = {"leading": 0, "trailing": 1, "both": 2}
 OUT_DTYPES = {"f32": 0, "bf16": 1}
 GEOM_PRECISIONS = {"fp32": 0, "fp64": 1}
-KERNELS = {0: "rows", 1: "pixels"}
+KERNELS = {0: "rows", 1: "pixels", 2: "intervals"}
 
 # every symbol include/dr.h declares (checked by the CPU tests)
 EXPORTS = ("dr_plan", "dr_plan_destroy", "dr_plan_get_info", "dr_plan_device_bytes",
@@ -50,7 +50,8 @@ class Geometry(ctypes.Structure):
 class PlanOptions(ctypes.Structure):
     _fields_ = [("out_dtype", ctypes.c_int32), ("geom_precision", ctypes.c_int32),
                 ("tile_cols", ctypes.c_int32), ("bin_groups", ctypes.c_int32),
-                ("force_pixels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("force_pixels", ctypes.c_int32), ("force_intervals", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -206,7 +207,8 @@ class Plan:
     """
 
     def __init__(self, geom, wires, edges, edge="leading", out_dtype="f32",
-                 geom_precision="fp32", tile_cols=0, bin_groups=0, force_pixels=False):
+                 geom_precision="fp32", tile_cols=0, bin_groups=0, force_pixels=False,
+                 force_intervals=False):
         L = lib()
         self._wires = np.ascontiguousarray(wires, dtype=np.float64)
         self._edges = np.ascontiguousarray(edges, dtype=np.float64)
@@ -220,6 +222,7 @@ class Plan:
         o.tile_cols = int(tile_cols)
         o.bin_groups = int(bin_groups)
         o.force_pixels = 1 if force_pixels else 0
+        o.force_intervals = 1 if force_intervals else 0
         h = ctypes.c_void_p()
         check(L.dr_plan(ctypes.byref(g), self._wires.ctypes.data_as(ctypes.c_void_p),
                         self._wires.shape[0], self._edges.ctypes.data_as(ctypes.c_void_p),
