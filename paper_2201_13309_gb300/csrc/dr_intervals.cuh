@@ -15,9 +15,9 @@
 // [e_j, e_{j+1}) that holds it.  Mass outside [e_0, e_B] is dropped.
 //
 // A CTA owns one row x 8 adjacent pixels x all K steps (image tile staged by
-// TMA as in the other kernels, depths of the 8 pixels in shared memory), one
-// warp per pixel.  The bins go through shared-memory windows of `window`
-// int64 accumulators per pixel; the lanes of a warp take the pixel's
+// TMA as in the other kernels, depths of the 8 pixels in shared memory); a
+// warp covers 4 steps x the 8 pixels.  The bins go through shared-memory
+// windows of `window` int64 accumulators per pixel; the threads take the
 // intervals in turn and add dI * phi(e) on the fixed-point grid 2^-30
 // (Phi(e_{j+1}) - Phi(e_j), so the parts of one interval add up to dI
 // exactly) with shared-memory atomics.  Integer sums do not depend on the
@@ -30,24 +30,46 @@
 
 namespace dr {
 
-constexpr double kIvScale = 1073741824.0;  // 2^30: fixed-point grid of the sums
+constexpr float kIvScale = 1073741824.f;  // 2^30: fixed-point grid of the sums
 
-// Phi(e) = round(dI * phi(e) * 2^30), phi(e) = clamp((e - lo) / (hi - lo), 0, 1)
-__device__ __forceinline__ long long iv_phi(int32_t e, int32_t lo, float inv_len, float dI) {
-  const float f = fminf(fmaxf(__fmul_rn((float)((long long)e - lo), inv_len), 0.f), 1.f);
-  return __float2ll_rn(__fmul_rn(__fmul_rn(dI, f), (float)kIvScale));
+// round(q * 2^30) for |q| < 2^31 without 64-bit conversions (those run on
+// the FP64 pipe): q = i + r with i = trunc(q) and r = q - i exact, and
+// r * 2^30 < 2^30 in magnitude
+__device__ __forceinline__ long long iv_fix(float q) {
+  const int i = __float2int_rz(q);
+  const int r = __float2int_rn(__fmul_rn(__fsub_rn(q, (float)i), kIvScale));
+  return (long long)i * (1ll << 30) + r;
 }
-__device__ __forceinline__ long long iv_phi(double e, double lo, double inv_len, float dI) {
-  const double f = fmin(fmax((e - lo) * inv_len, 0.0), 1.0);
-  return __double2ll_rn((double)dI * f * kIvScale);
+// Phi(e) = round(dI * phi(e) * 2^30), phi(e) = clamp((e - lo) / (hi - lo), 0, 1);
+// edges at or beyond an end give 0 or dI * 2^30 exactly
+__device__ __forceinline__ long long iv_phi(int32_t e, int32_t lo, int32_t hi, float inv_len,
+                                            int dI) {
+  if (e <= lo) return 0;
+  if (e >= hi) return (long long)dI * (1ll << 30);
+  const float f = fminf(__fmul_rn(__uint2float_rn((uint32_t)e - (uint32_t)lo), inv_len), 1.f);
+  return iv_fix(__fmul_rn((float)dI, f));
+}
+__device__ __forceinline__ long long iv_phi(double e, double lo, double hi, double inv_len,
+                                            int dI) {
+  if (e <= lo) return 0;
+  if (e >= hi) return (long long)dI * (1ll << 30);
+  const double f = fmin((e - lo) * inv_len, 1.0);
+  return __double2ll_rn((double)dI * f * (double)kIvScale);
 }
 __device__ __forceinline__ float iv_inv_len(int32_t lo, int32_t hi) {
-  return __frcp_rn((float)((long long)hi - lo));
+  return __frcp_rn(__uint2float_rn((uint32_t)hi - (uint32_t)lo));
 }
 __device__ __forceinline__ double iv_inv_len(double lo, double hi) { return 1.0 / (hi - lo); }
+// accumulator (units of 2^-30) to FP32 with one rounding: hi * 4 is exact
+// (|hi| < 2^24 for any 16-bit scan of fewer than 65536 steps)
+__device__ __forceinline__ float iv_value(long long a) {
+  const int hi = (int)(a >> 32);
+  const uint32_t lo = (uint32_t)a;
+  return __fmaf_rn(__uint2float_rn(lo), 1.f / kIvScale, __fmul_rn((float)hi, 4.f));
+}
 
 template <class Geo, class OutT, bool kTma>
-__global__ void __launch_bounds__(256) intervals_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ CUtensorMap tmap,
                                                         const uint16_t *__restrict__ img,
                                                         OutT *__restrict__ out, const Consts c,
                                                         const Tuning t, int pixel_groups,
@@ -72,12 +94,21 @@ __global__ void __launch_bounds__(256) intervals_kernel(const __grid_constant__ 
     if (tid == 0) mbar_init(bar, 1);
   }
   stage_tile<kTma>(&tmap, img, simg, bar, c, t, row, c0);
-  {  // depths of the tile: thread -> pixel tid % 8, steps tid / 8, + NT / 8, ...
-    const int lc = tid % TC;
+  // a warp covers 4 steps x the 8 pixels (lane = 8 * step + pixel), so its
+  // shared-memory accesses to the [step][pixel] arrays are contiguous
+  const int warp = tid >> 5, lane = tid & 31, nwarps = NT >> 5;
+  const int lc = lane & (TC - 1), s4 = warp * 4 + (lane >> 3), S = nwarps * 4;
+  {  // depths of the tile: steps s4, s4 + S, ... of pixel lc, two at a time
     if (lc < ncols) {
       const auto g = Geo::group(c, pixel_groups ? row * c.W + c0 + lc : row);
       const auto *steps = Geo::steps(c);
-      for (int k = tid / TC; k < K; k += NT / TC) spos[k * TC + lc] = Geo::depth(g, steps[k], c);
+      for (int k = s4; k < K; k += 2 * S) {
+        const int k2 = min(k + S, K - 1);
+        pos_t d0, d1;
+        Geo::depth2(g, steps[k], steps[k2], c, d0, d1);
+        spos[k * TC + lc] = d0;
+        if (k + S < K) spos[(k + S) * TC + lc] = d1;
+      }
     }
   }
   for (int j = tid; j <= B; j += NT) sedge[j] = Geo::edge(c, j);
@@ -87,13 +118,24 @@ __global__ void __launch_bounds__(256) intervals_kernel(const __grid_constant__ 
     if (__syncthreads_or(late)) return;
   }
 
-  const int warp = tid >> 5, lane = tid & 31, nwarps = NT >> 5;
   const bool rev = c.reverse != 0;
   const float sign = c.out_sign;
   const size_t plane = (size_t)c.H * c.W;
   const bool acc_out = c.accumulate != 0;
-  // number of edges e_i <= x (0..B+1)
+  // number of edges e_i <= x (0..B+1): a guess from the mean bin width,
+  // checked against its two neighbouring edges and moved by up to two edges;
+  // a binary search when that does not settle it (uneven bins)
+  const pos_t e0 = sedge[0];
+  const float inv_w = (float)B / (float)(sedge[B] - e0);
   auto count_le = [&](pos_t x) {
+    int g = (int)fminf(fmaxf((float)(x - e0) * inv_w + 1.f, 0.f), (float)(B + 1));
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+      const bool below_ok = g == 0 || sedge[g - 1] <= x;   // e_{g-1} <= x
+      const bool above_ok = g == B + 1 || sedge[g] > x;    // e_g > x
+      if (below_ok && above_ok) return g;
+      g += below_ok ? 1 : -1;
+    }
     int lo = 0, hi = B + 1;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
@@ -108,40 +150,36 @@ __global__ void __launch_bounds__(256) intervals_kernel(const __grid_constant__ 
     for (int i = tid; i < nwin; i += NT) acc[i] = 0ull;
     __syncthreads();
     const pos_t ewlo = sedge[wb0], ewhi = sedge[wb1];
-    for (int lc = warp; lc < ncols; lc += nwarps) {
-      for (int m = lane; m < K - 1; m += 32) {
-        const int ia = rev ? K - 1 - m : m, ib = rev ? K - 2 - m : m + 1;
-        const int dI = (int)simg[ia * TC + lc] - (int)simg[ib * TC + lc];
-        if (dI == 0) continue;
-        const pos_t a = spos[m * TC + lc], b = spos[(m + 1) * TC + lc];
-        const pos_t lo = a < b ? a : b, hi = a < b ? b : a;
-        if (lo >= ewhi || hi < ewlo) continue;  // nothing in this window
-        const int u = count_le(lo);
-        if (!(hi > lo)) {  // zero length: the bin [e_j, e_{j+1}) holding lo
-          const int j = u - 1;
-          if (j >= wb0 && j < wb1)
-            atomicAdd(&acc[(j - wb0) * TC + lc],
-                      (unsigned long long)((long long)dI * (long long)kIvScale));
-          continue;
-        }
-        const auto inv = iv_inv_len(lo, hi);
-        const float dIf = (float)dI;
-        int j = max(u - 1, wb0);
-        long long p0 = iv_phi(sedge[j], lo, inv, dIf);
-        for (; j < wb1 && sedge[j] < hi; ++j) {
-          const long long p1 = iv_phi(sedge[j + 1], lo, inv, dIf);
-          if (p1 != p0) atomicAdd(&acc[(j - wb0) * TC + lc], (unsigned long long)(p1 - p0));
-          p0 = p1;
-        }
+    // intervals m = s4, s4 + S, ... of pixel lc
+    for (int m = s4; m < K - 1 && lc < ncols; m += S) {
+      const int ia = rev ? K - 1 - m : m, ib = rev ? K - 2 - m : m + 1;
+      const int dI = (int)simg[ia * TC + lc] - (int)simg[ib * TC + lc];
+      if (dI == 0) continue;
+      const pos_t a = spos[m * TC + lc], b = spos[(m + 1) * TC + lc];
+      const pos_t lo = a < b ? a : b, hi = a < b ? b : a;
+      if (lo >= ewhi || hi < ewlo) continue;  // nothing in this window
+      const int u = count_le(lo);
+      if (!(hi > lo)) {  // zero length: the bin [e_j, e_{j+1}) holding lo
+        const int j = u - 1;
+        if (j >= wb0 && j < wb1)
+          atomicAdd(&acc[(j - wb0) * TC + lc], (unsigned long long)((long long)dI * (1ll << 30)));
+        continue;
+      }
+      const auto inv = iv_inv_len(lo, hi);
+      int j = max(u - 1, wb0);
+      long long p0 = iv_phi(sedge[j], lo, hi, inv, dI);
+      for (; j < wb1 && sedge[j] < hi; ++j) {
+        const long long p1 = iv_phi(sedge[j + 1], lo, hi, inv, dI);
+        if (p1 != p0) atomicAdd(&acc[(j - wb0) * TC + lc], (unsigned long long)(p1 - p0));
+        p0 = p1;
       }
     }
     __syncthreads();
     for (int i = tid; i < nwin; i += NT) {
-      const int jj = i / TC, lc = i - jj * TC;
-      if (lc >= ncols) continue;
-      OutT *o = out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + lc;
-      const float v =
-          __fmul_rn(sign, (float)((double)(long long)acc[i] * (1.0 / kIvScale)));
+      const int jj = i / TC, px = i - jj * TC;
+      if (px >= ncols) continue;
+      OutT *o = out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + px;
+      const float v = __fmul_rn(sign, iv_value((long long)acc[i]));
       st_cs(o, acc_out ? __fadd_rn(out_load(o), v) : v);
     }
     __syncthreads();  // the window's accumulators are reused

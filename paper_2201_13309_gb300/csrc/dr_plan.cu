@@ -414,7 +414,7 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
     t.ppt = 1;
     t.tile_cols = kIntervalTile;
     t.bin_groups = 1;
-    p->threads = 256;
+    p->threads = 512;  // two warps per pixel
     if (K > 65535) {
       delete p;
       set_error("dr_plan: the interval kernel takes at most 65535 steps");
