@@ -124,6 +124,40 @@ def test_per_pixel_launch_shapes_agree(rotated_ragged, tc, bg):
     assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
 
 
+def _lit_scan(geom, wires, seed, lo_um, hi_um, width_um):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = O.depths(geom, wires)
+    scat = synth.Scatterers(rng.uniform(d.min(), d.max(), 4), rng.uniform(500.0, 5000.0, 4))
+    images = synth.poisson_u16(rng, synth.expected_counts(geom, wires, scat, background=25.0))
+    return synth.Scan(geom, wires, synth.bin_edges(lo_um, hi_um, width_um), images)
+
+
+def test_wire_axis_oblique_to_beam():
+    """Wire axis tilted 20 degrees toward the beam: the projected frame
+    shrinks the beam by cos(angle) and detector rows no longer run along the
+    axis (per-pixel depths)."""
+    g = synth.detector_geometry(8, 48, roi_origin=(1000, 1000), det_rows=2048, det_cols=2048)
+    a = np.deg2rad(20.0)
+    g = dict(g, wire_axis=[np.cos(a), 0.0, np.sin(a)])
+    sc = _lit_scan(g, synth.wire_path(41), 31, 0.0, 65.0, 1.0)
+    plan, out = run(sc)
+    assert plan.info()["kernel"] == "pixels"
+    assert_parity(out.cpu().numpy(), ref_of(sc), sc.images)
+
+
+def test_non_uniform_wire_steps():
+    """Steps of 0.3 to 2 um drawn at random along the beam."""
+    g = synth.detector_geometry(8, 64, roi_origin=(1000, 1000), det_rows=2048, det_cols=2048)
+    rng = np.random.Generator(np.random.PCG64(32))
+    z = np.cumsum(rng.uniform(0.3, 2.0, 41)) * 1e-3
+    w = synth.wire_path(41)
+    w[:, 2] = w[0, 2] + z - z[0]
+    sc = _lit_scan(g, w, 33, 0.0, 70.0, 0.5)
+    plan, out = run(sc)
+    assert plan.info()["kernel"] == "rows"
+    assert_parity(out.cpu().numpy(), ref_of(sc), sc.images)
+
+
 @pytest.mark.parametrize("edge", ["leading", "trailing"])
 def test_edges_and_reversed_travel(edge):
     sc = synth.tiny_scan(5, rows=16, cols=40, K=25)
