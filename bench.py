@@ -45,23 +45,30 @@ PROFILE_TRAFFIC = {
     "rows": os.path.join(ROOT, "profiles", "rows_kernel_full_detector_traffic.txt"),
     "pixels": os.path.join(ROOT, "profiles", "pixels_kernel_rotated_detector_traffic.txt"),
 }
-# the rows kernel's code ends where the persistent batch kernel begins
+# the rows kernel's code ends where the persistent batch kernel begins; the
+# per-pixel kernel's own section follows the batch kernel
 ROWS_KERNEL_END = "// ------------------------------------------------- persistent batch kernel ---"
+PIXELS_KERNEL_BEGIN = "// ------------------------------------------------------- pixels kernel ---"
+PIXELS_KERNEL_END = "// ------------------------------------------------ small helper kernels ---"
 
 
 def kernel_source_hash(kernel="rows", device_src=None, tables_src=None):
-    """Hash of the code a kernel is built from: for the rows kernel the device
-    header up to the persistent batch kernel (helpers, depth model, row
-    tables, rows_tile, rows_kernel), for the per-pixel kernel the whole device
-    header; both with the table layouts."""
+    """Hash of the code a kernel is built from: the device header up to the
+    persistent batch kernel (helpers, depth model, row tables, rows_tile,
+    rows_kernel), for the per-pixel kernel also its own section, and the
+    table layouts."""
     csrc = os.path.join(ROOT, "paper_2201_13309_gb300", "csrc")
     if device_src is None:
         device_src = open(os.path.join(csrc, "dr_device.cuh"), "rb").read()
     if tables_src is None:
         tables_src = open(os.path.join(csrc, "dr_tables.h"), "rb").read()
-    cut = device_src.find(ROWS_KERNEL_END.encode()) if kernel == "rows" else -1
     h = hashlib.sha256()
+    cut = device_src.find(ROWS_KERNEL_END.encode())
     h.update(device_src[:cut] if cut >= 0 else device_src)
+    if kernel == "pixels":
+        b = device_src.find(PIXELS_KERNEL_BEGIN.encode())
+        e = device_src.find(PIXELS_KERNEL_END.encode())
+        h.update(device_src[b:e] if 0 <= b < e else device_src)
     h.update(tables_src)
     return h.hexdigest()[:16]
 

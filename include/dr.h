@@ -185,8 +185,10 @@ dr_status dr_reconstruct_streamed(const dr_plan_t *plan, const uint16_t *h_image
 /* ---- Pixel selection (the paper's pixel-percentage experiment, Sec. IV-A) --
  * Only some pixels carry signal (diffraction spots); these calls reconstruct
  * only the selected ones into a compacted output.
- * dr_pixel_activity: d_activity[p] = sum_k |I_k(p) - I_{k+1}(p)| (exact,
- *   stored as float; K <= 32768) for the [K][rows][cols] stack, p row-major.
+ * dr_pixel_activity: d_activity[p] = sum_k |I_k(p) - I_{k+1}(p)| for the
+ *   [K][rows][cols] stack, p row-major; summed exactly in 32-bit integers
+ *   (K <= 32768) and stored as float, i.e. exact up to 2^24 and rounded to
+ *   nearest above (possible only for K > 257).
  * dr_select_pixels: the indices p (0..n-1) with d_activity[p] >= threshold,
  *   in increasing order, into d_index (room for n entries); the number of them
  *   into the device int32 *d_count.  Needs dr_select_scratch_bytes(n) bytes of

@@ -919,8 +919,12 @@ __global__ void __launch_bounds__(256) selected_kernel(const Consts c, int kerne
   const auto *steps = Geo::steps(c);
   int k = 0;
   pos_t t0 = Geo::depth(g, steps[0], c), t1 = Geo::depth(g, steps[1], c);
+  // bins at or above the last depth are zero, as in pixels_kernel
+  const pos_t tlast = Geo::depth(g, steps[K - 1], c);
+  const float zero = __fmul_rn(sign, 0.f);
   auto inv = Geo::inv_len(t0, t1);
   float Ik = I0, Ik1 = px(1), Fp = 0.f;
+  pos_t ep = 0;
   for (int j = 0; j <= B; ++j) {
     const pos_t e = Geo::edge(c, j);
     while (k < K - 2 && t1 < e) {
@@ -934,10 +938,11 @@ __global__ void __launch_bounds__(256) selected_kernel(const Consts c, int kerne
     const float f = Geo::frac(e, t0, inv);
     const float F = __fmaf_rn(f, __fsub_rn(Ik, Ik1), __fsub_rn(I0, Ik));
     if (j > 0) {
-      st_cs(o, __fmul_rn(sign, __fsub_rn(F, Fp)));
+      st_cs(o, ep < tlast ? __fmul_rn(sign, __fsub_rn(F, Fp)) : zero);
       o += n;
     }
     Fp = F;
+    ep = e;
   }
 }
 
@@ -969,11 +974,12 @@ __device__ __forceinline__ int warp_lower_bound(const int32_t *idx, int n, int t
 }
 
 // Listed pixels of row-shared geometry, staged like rows_tile: one CTA per
-// (row, column tile); tiles without listed pixels load nothing; each thread
-// streams the bins of one listed pixel from shared memory into the compacted
-// output out[j * n + i].  Needs the plan's row tables; TMA only.
+// (row, column tile), the tile copied while its index range is searched; the
+// listed pixels' bins are split over the threads, which stream them from
+// shared memory into the compacted output out[j * n + i].  Needs the plan's
+// row tables; TMA only.
 template <class OutT>
-__global__ void __launch_bounds__(256) selected_rows_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(512) selected_rows_kernel(const __grid_constant__ CUtensorMap tmap,
                                                             const Consts c, const Tuning t,
                                                             const int32_t *__restrict__ idx, int n,
                                                             OutT *__restrict__ out) {
@@ -986,54 +992,61 @@ __global__ void __launch_bounds__(256) selected_rows_kernel(const __grid_constan
   int2 *stab0 = reinterpret_cast<int2 *>(smem + 128 + align16((size_t)Kpad * TC * 2) +
                                          align16((size_t)K * sizeof(int32_t)));
   const int row = blockIdx.y, c0 = blockIdx.x * TC;
-  const int tid = threadIdx.x;
-  if (tid < 32) {
-    const int first = row * c.W + c0;
-    const int lo = warp_lower_bound(idx, n, first);
-    const int hi = warp_lower_bound(idx, n, first + min(TC, c.W - c0));
-    if (tid == 0) {
-      range[0] = lo;
-      range[1] = hi;
-      mbar_init(bar, 1);
-    }
-  }
-  __syncthreads();
-  const int lo = range[0], hi = range[1];
-  if (lo >= hi) return;  // nothing listed in this tile
-  const int2 *grow = c.tab + (size_t)row * c.tab_stride;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // the tile and the row table are requested first; meanwhile warps 0 and 1
+  // find the tile's first and end positions in the index list
   if (tid == 0) {
+    mbar_init(bar, 1);
     const uint32_t tab_bytes = (uint32_t)c.tab_stride * 8u;
     mbar_expect_tx(bar, (uint32_t)(Kpad * TC * 2) + tab_bytes);
     for (int ch = 0; ch < t.nchunks; ++ch)
       tma_load_3d(simg + (size_t)ch * t.kc * TC, &tmap, bar, c0, row, ch * t.kc);
-    bulk_load_1d(stab0, grow, tab_bytes, bar);
+    bulk_load_1d(stab0, c.tab + (size_t)row * c.tab_stride, tab_bytes, bar);
   }
+  if (warp < 2) {
+    const int first = row * c.W + c0;
+    const int r = warp_lower_bound(idx, n, warp == 0 ? first : first + min(TC, c.W - c0));
+    if ((tid & 31) == 0) range[warp] = r;
+  }
+  __syncthreads();
   const bool late = !mbar_wait_bounded(bar, 0, c.err);
   if (__syncthreads_or(late)) return;
+  const int lo = range[0], hi = range[1];
+  if (lo >= hi) return;  // nothing listed in this tile (its copies are complete)
   const int2 nz = stab0[0];
   const int2 *stab = stab0 + 1;
   const float sign = c.out_sign, zero = __fmul_rn(sign, 0.f);
   const bool rev = c.reverse != 0;
-  for (int i = lo + tid; i < hi; i += blockDim.x) {
+  // the m listed pixels x G bin groups (G the largest power of two with
+  // m * G <= threads); consecutive threads take consecutive listed pixels,
+  // so the stores of one bin are contiguous
+  const int m = hi - lo, NT = blockDim.x;
+  int G = 1;
+  while (G < 32 && m * G * 2 <= NT) G *= 2;
+  for (int sidx = tid; sidx < m * G; sidx += NT) {
+    const int il = sidx % m, g = sidx / m, i = lo + il;
+    const int jb = (int)((long long)B * g / G), je = (int)((long long)B * (g + 1) / G);
     const int lc = idx[i] - row * c.W - c0;
     auto pxs = [&](int k) { return biased(simg[(size_t)(rev ? K - 1 - k : k) * TC + lc]); };
     const float I0 = pxs(0);
-    OutT *o = out + i;
-    for (int j = 0; j < nz.x; ++j, o += n) st_cs(o, zero);
-    if (nz.x < nz.y) {
+    OutT *o = out + (size_t)jb * n + i;
+    int j = jb;
+    for (; j < min(je, nz.x); ++j, o += n) st_cs(o, zero);
+    const int a = max(jb, nz.x), b = min(je, nz.y);
+    if (a < b) {
       auto evalF = [&](int2 kf) {
         const float x = pxs(kf.x), y = pxs(kf.x + 1);
         return __fmaf_rn(__int_as_float(kf.y), __fsub_rn(x, y), __fsub_rn(I0, x));
       };
-      float Fp = evalF(stab[nz.x]);
+      float Fp = evalF(stab[a]);
 #pragma unroll 4
-      for (int j = nz.x; j < nz.y; ++j, o += n) {
+      for (j = a; j < b; ++j, o += n) {
         const float F = evalF(stab[j + 1]);
         st_cs(o, __fmul_rn(sign, __fsub_rn(F, Fp)));
         Fp = F;
       }
     }
-    for (int j = max(nz.y, nz.x); j < B; ++j, o += n) st_cs(o, zero);
+    for (j = max(j, max(jb, nz.y)); j < je; ++j, o += n) st_cs(o, zero);
   }
 }
 }  // namespace dr

@@ -34,7 +34,7 @@ def test_selection_sweep(rotate):
     plan = dr.Plan(sc.geom, sc.wires, sc.edges)
     full = plan.reconstruct(img).reshape(sc.B, -1)
     flat = act.reshape(-1)
-    for pct in (25, 50, 70, 100):   # sparse lists walk, dense ones (>= 60%) are staged
+    for pct in (3, 25, 50, 70, 100):   # lists under 60% walk, denser ones are staged
         thr = float(np.percentile(want, 100 - pct)) if pct < 100 else -1.0
         idx, n = dr.select_pixels(flat, thr)
         ref_idx = np.nonzero(want.reshape(-1) >= thr)[0]
@@ -42,6 +42,22 @@ def test_selection_sweep(rotate):
         out = plan.reconstruct_selected(img, idx, n)
         torch.cuda.synchronize()
         assert torch.equal(out.view(torch.int32), full[:, idx.long()].view(torch.int32))
+
+
+@pytest.mark.parametrize("rows,cols,K", [(3, 64, 7), (5, 37, 7), (2, 8, 2), (4, 40, 402)])
+def test_activity_exact(rows, cols, K):
+    """Sum |dI| with 16-byte loads (pixel count a multiple of 8) and with the
+    2-pixel form (odd count), step counts with and without a tail of the
+    4-step unroll, extreme values (0 / 65535 alternating): the exact integer
+    sum rounded once to FP32 (exact below 2^24; the extreme pixels of the
+    402-step stack sum to 26.3 M)."""
+    rng = np.random.Generator(np.random.PCG64(rows * cols + K))
+    im = rng.integers(0, 65536, (K, rows, cols), dtype=np.uint16)
+    im[::2, 0, :4] = 0
+    im[1::2, 0, :4] = 65535
+    act = dr.pixel_activity(_dev(im)).cpu().numpy()
+    want = np.abs(np.diff(im.astype(np.int64), axis=0)).sum(0)
+    assert np.array_equal(act, want.astype(np.float32))
 
 
 def test_selection_edge_cases():
