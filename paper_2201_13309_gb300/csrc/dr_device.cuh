@@ -686,7 +686,6 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks) pixels_kernel(cons
   using pos_t = typename Geo::pos_t;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-  int2 *span = reinterpret_cast<int2 *>(smem + 16);  // per slab, at most 8 slabs
   uint16_t *simg = reinterpret_cast<uint16_t *>(smem + 128);
   const int TC = t.tile_cols, K = c.K, B = c.B, G = t.bin_groups;
   const int Kpad = t.kc * t.nchunks;
@@ -722,27 +721,42 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks) pixels_kernel(cons
   for (int j = tid; j <= B; j += NT) sedge[j] = Geo::edge(c, j);
   __syncthreads();  // also makes the mbarrier initialisation visible
   auto pos = [&](int k) { return spos[k * TC + lc]; };
-  if (tid < max(TC, 32)) {  // whole warps holding the shares 0 of all slabs
-    const pos_t lo_d = group_min(valid ? pos(0) : sedge[B], SW);
-    const pos_t hi_d = group_max(valid ? pos(K - 1) : sedge[0], SW);
-    int lo = 0, hi = B;
-    while (lo < hi) {  // first j with e_{j+1} > min d_0
-      const int mid = (lo + hi) >> 1;
-      if (sedge[mid + 1] > lo_d) hi = mid; else lo = mid + 1;
+  // Counts on the sorted edges and depths, guessed by linear interpolation
+  // (uniform bins, near-uniform depth steps), checked against the two
+  // neighbours and moved by up to two places; a binary search otherwise.
+  // below(i) must hold for a prefix of [0, n) and fail after it.
+  auto count_prefix = [](float guess, int n, auto below) {
+    int g = (int)fminf(fmaxf(guess, 0.f), (float)n);
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+      const bool lo_ok = g == 0 || below(g - 1);
+      const bool hi_ok = g == n || !below(g);
+      if (lo_ok && hi_ok) return g;
+      g += lo_ok ? 1 : -1;
     }
-    const int jlo = lo;
-    hi = B;
-    while (lo < hi) {  // first j with e_j >= max d_{K-1}
+    int lo = 0, hi = n;
+    while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (sedge[mid] < hi_d) lo = mid + 1; else hi = mid;
+      if (below(mid)) lo = mid + 1; else hi = mid;
     }
-    if (share == 0 && sl == 0) span[slab] = make_int2(jlo, lo);
-  }
-  __syncthreads();
+    return lo;
+  };
+  const pos_t e0 = sedge[0];
+  const float bins_per_pos = (float)B / (float)(sedge[B] - e0);
+  // the slab's data span [jlo, jhi): bin j can hold data for some pixel of
+  // the slab only if e_{j+1} > min d_0 and e_j < max d_{K-1}; every warp
+  // holds whole slabs, so each finds its own
+  const pos_t lo_d = group_min(valid ? pos(0) : sedge[B], SW);
+  const pos_t hi_d = group_max(valid ? pos(K - 1) : sedge[0], SW);
+  const int n_le = count_prefix((float)(lo_d - e0) * bins_per_pos + 1.f, B + 1,
+                                [&](int i) { return !(sedge[i] > lo_d); });
+  const int n_lt = count_prefix((float)(hi_d - e0) * bins_per_pos + 1.f, B + 1,
+                                [&](int i) { return sedge[i] < hi_d; });
+  const int jlo = min(max(n_le - 1, 0), B);
+  const int2 sp = make_int2(jlo, max(min(n_lt, B), jlo));
   if constexpr (kTma) {
     if (!mbar_wait_bounded(bar, 0, c.err)) return;
   }
-  const int2 sp = span[slab];
   const float sign = c.out_sign, zero = __fmul_rn(sign, 0.f);
   const size_t plane = (size_t)c.H * c.W;
   const bool acc = c.accumulate != 0;
@@ -782,13 +796,11 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks) pixels_kernel(cons
   const int istep = rev ? -TC : TC;
   auto spx = [&](int k) { return biased(ip[k * istep]); };
   // k = last step below e_jb, clamped to an interval
-  pos_t e0 = sedge[jb];
-  int lo = 0, hi = K;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (pos(mid) < e0) lo = mid + 1; else hi = mid;
-  }
-  int k = min(max(lo - 1, 0), K - 2);
+  pos_t eb = sedge[jb];
+  const int n_below = count_prefix(
+      (float)(eb - tfirst) * ((float)(K - 1) / (float)(tlast - tfirst)) + 1.f, K,
+      [&](int i) { return pos(i) < eb; });
+  int k = min(max(n_below - 1, 0), K - 2);
   pos_t t0 = pos(k), t1 = pos(k + 1);
   auto inv = Geo::inv_len(t0, t1);
   const float I0 = spx(0);
@@ -808,16 +820,16 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks) pixels_kernel(cons
     }
     return __fmaf_rn(Geo::frac(e, t0, inv), dI, base);
   };
-  float Fp = F_at(e0);
+  float Fp = F_at(eb);
   OutT *o = o0 + (size_t)jb * plane;
   if (acc) {
     for (int j = jb; j < je; ++j, o += plane) {
       const pos_t e1 = sedge[j + 1];
       const float F = F_at(e1);
       const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
-      if (e1 > tfirst && e0 < tlast) st_cs(o, __fadd_rn(out_load(o), v));
+      if (e1 > tfirst && eb < tlast) st_cs(o, __fadd_rn(out_load(o), v));
       Fp = F;
-      e0 = e1;
+      eb = e1;
     }
   } else {
     // below d_0 both edges give F = 0 exactly, so only the upper test is
@@ -827,9 +839,9 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks) pixels_kernel(cons
       const pos_t e1 = sedge[j + 1];
       const float F = F_at(e1);
       const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
-      st_cs(o, e0 < tlast ? v : zero);
+      st_cs(o, eb < tlast ? v : zero);
       Fp = F;
-      e0 = e1;
+      eb = e1;
     }
   }
 }
