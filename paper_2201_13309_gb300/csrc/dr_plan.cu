@@ -677,7 +677,7 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t 
   double travel = 0.0;
   bool repeated = false;
   {
-    V3 ax = v3(g->wire_axis), bd = v3(g->beam_dir), O = v3(g->beam_origin);
+    V3 ax = v3(g->wire_axis), bd = v3(g->beam_dir);
     if (norm(ax) > 0 && norm(bd) > 0 && finite3(wires) && finite3(wires + 3 * (K - 1))) {
       ax = (1.0 / norm(ax)) * ax;
       bd = (1.0 / norm(bd)) * bd;
