@@ -85,8 +85,13 @@ typedef struct {
 typedef struct {
   int32_t out_dtype;        /* DR_OUT_F32 (default) or DR_OUT_BF16 */
   int32_t geom_precision;   /* DR_GEOM_FP32 (default): per-step depth in FP32
-                               on FP64 per-pixel constants; DR_GEOM_FP64: the
-                               whole depth computation in FP64 on the GPU */
+                               on FP64 per-pixel constants, positions on a
+                               grid of 2^-fixed_shift mm (a few units of
+                               error, so an interval of L units may move
+                               about 8/L of its difference across a bin edge:
+                               below the 1e-4 bar for steps above ~60 nm at
+                               the beamline scale); DR_GEOM_FP64: the whole
+                               depth computation in FP64 on the GPU */
   int32_t tile_cols;        /* pixels per CTA along a row; 0 = tuned */
   int32_t bin_groups;       /* warps-groups splitting the bins; 0 = tuned */
   int32_t force_pixels;     /* 1: use the per-pixel kernel even when all

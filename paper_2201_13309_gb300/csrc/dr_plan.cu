@@ -342,7 +342,10 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   }
   const double scale = std::ldexp(1.0, shift);
   if (minstep == 1e300) minstep = 0.0;  // interval kernel, no nonzero step seen
-  if (P > 0 && !intervals && minstep * scale < 64.0) {
+  // FP32 geometry positions carry a few grid units of error, so an interval
+  // must span many units (zero-length intervals are exact); FP64 geometry
+  // computes positions and fractions in FP64
+  if (P > 0 && opt.geom_precision == DR_GEOM_FP32 && minstep > 0.0 && minstep * scale < 64.0) {
     set_error("dr_plan: depth steps (%.3g mm) too small for the fixed-point grid", minstep);
     return DR_ERR_UNSUPPORTED;
   }
@@ -710,7 +713,16 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t 
     return plan_parts(true, g, wires, K, edges, B, opt, one, travel, out);
   dr_status st = plan_parts(false, g, wires, K, edges, B, opt, starts, travel, out);
   if (st == DR_ERR_NONMONOTONIC)  // depth runs against its wire run somewhere
-    st = plan_parts(true, g, wires, K, edges, B, opt, one, travel, out);
+    return plan_parts(true, g, wires, K, edges, B, opt, one, travel, out);
+  if (st == DR_ERR_UNSUPPORTED && !(opt && opt->force_pixels)) {
+    // outside what the running-sum kernels take (depth steps too fine for
+    // their fixed-point grid, tile memory): the interval kernel needs neither;
+    // if it cannot take the scan either, the first reason is reported
+    char first[sizeof(g_msg)];
+    std::memcpy(first, g_msg, sizeof(g_msg));
+    if (plan_parts(true, g, wires, K, edges, B, opt, one, travel, out) == DR_OK) return DR_OK;
+    std::memcpy(g_msg, first, sizeof(g_msg));
+  }
   return st;
 }
 

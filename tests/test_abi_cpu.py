@@ -72,6 +72,9 @@ def test_plan_rejects_bad_inputs(lib):
     assert _plan_status(g, back, e, edge="both")[0] == 2         # both edges, same
     g3 = dict(g, rows=-1)
     assert _plan_status(g3, w, e)[0] == 1
+    fine = synth.wire_path(5, dz=1e-10)                          # 0.1 pm steps
+    st, msg = _plan_status(g, fine, e)
+    assert st == 8 and "too small" in msg                        # FP32 grid limit
     # Repeated positions and depths running against the wire's travel are
     # valid plans (the interval kernel): they get past validation to the
     # device allocation, tested in test_gpu_intervals.py.
