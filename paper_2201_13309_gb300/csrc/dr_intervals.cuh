@@ -146,8 +146,9 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
 
   for (int wb0 = 0; wb0 < B; wb0 += window) {
     const int wb1 = min(wb0 + window, B);
-    const int nwin = (wb1 - wb0) * TC;
-    for (int i = tid; i < nwin; i += NT) acc[i] = 0ull;
+    const int nwin = (wb1 - wb0) * TC;  // even: 8 accumulators per bin
+    for (int i = tid; i < nwin / 2; i += NT)
+      reinterpret_cast<ulonglong2 *>(acc)[i] = make_ulonglong2(0ull, 0ull);
     __syncthreads();
     const pos_t ewlo = sedge[wb0], ewhi = sedge[wb1];
     // intervals m = s4, s4 + S, ... of pixel lc
@@ -175,12 +176,27 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
       }
     }
     __syncthreads();
-    for (int i = tid; i < nwin; i += NT) {
-      const int jj = i / TC, px = i - jj * TC;
-      if (px >= ncols) continue;
-      OutT *o = out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + px;
-      const float v = __fmul_rn(sign, iv_value((long long)acc[i]));
-      st_cs(o, acc_out ? __fadd_rn(out_load(o), v) : v);
+    if (!acc_out && ncols == TC && c.W % 4 == 0 &&
+        ((uintptr_t)out & (4 * sizeof(OutT) - 1)) == 0) {
+      // 4 pixels per thread: two 16-byte shared loads, one vector store
+      for (int q = tid; q < nwin / 4; q += NT) {
+        const int jj = q >> 1, half = q & 1;
+        const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(acc)[2 * q];
+        const ulonglong2 b = reinterpret_cast<const ulonglong2 *>(acc)[2 * q + 1];
+        OutT *o = out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + 4 * half;
+        st_cs4(o, __fmul_rn(sign, iv_value((long long)a.x)),
+               __fmul_rn(sign, iv_value((long long)a.y)),
+               __fmul_rn(sign, iv_value((long long)b.x)),
+               __fmul_rn(sign, iv_value((long long)b.y)));
+      }
+    } else {
+      for (int i = tid; i < nwin; i += NT) {
+        const int jj = i / TC, px = i - jj * TC;
+        if (px >= ncols) continue;
+        OutT *o = out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + px;
+        const float v = __fmul_rn(sign, iv_value((long long)acc[i]));
+        st_cs(o, acc_out ? __fadd_rn(out_load(o), v) : v);
+      }
     }
     __syncthreads();  // the window's accumulators are reused
   }
