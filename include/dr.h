@@ -229,6 +229,15 @@ dr_status dr_plan_depths(const dr_plan_t *plan, int32_t r0, int32_t nrows,
  * wait ran out).  Synchronizes the device.  DR_OK or DR_ERR_TIMEOUT. */
 dr_status dr_plan_check(const dr_plan_t *plan);
 
+/* Failure-path diagnostic (no counterpart in the paper): launches one CTA on
+ * stream whose barrier is never completed, so its bounded wait (the form the
+ * reconstruction kernels use for their tile copies) runs out after wait_ms
+ * milliseconds (0 < wait_ms <= 2000); it records the timeout code in the
+ * caller's device word *d_status and returns, leaving the device usable.
+ * Synchronizes the stream; returns DR_ERR_TIMEOUT when the timeout was
+ * recorded (the expected outcome), DR_OK if the wait completed. */
+dr_status dr_selftest_wait_timeout(int32_t *d_status, double wait_ms, dr_stream_t stream);
+
 /* ---- Many scans in one persistent launch ---------------------------------
  * A batch reconstructs several scans (each with its own plan, image stack and
  * output; different ROI sizes, step and bin counts) in ONE launch of a

@@ -357,6 +357,48 @@ extern "C" dr_status dr_plan_check(const dr_plan_t *p) {
   return DR_OK;
 }
 
+// ------------------------------------------------ failure-path diagnostic ---
+namespace dr {
+// One CTA whose barrier nothing arrives at: the bounded wait runs out after
+// limit_ns, the timeout code goes to *err, and every thread returns.
+__global__ void wait_probe_kernel(int32_t *err, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(&bar, 0)) {
+    if (global_ns() - t0 > limit_ns) {
+      if (threadIdx.x == 0) atomicExch(err, kDevTmaTimeout);
+      return;
+    }
+  }
+}
+}  // namespace dr
+
+extern "C" dr_status dr_selftest_wait_timeout(int32_t *d_status, double wait_ms,
+                                              dr_stream_t stream) {
+  if (!d_status || !(wait_ms > 0.0) || wait_ms > 2000.0) {
+    set_error("dr_selftest_wait_timeout: need a status word and 0 < wait_ms <= 2000");
+    return DR_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return cuda_fail("dr_selftest_wait_timeout: clear", e);
+  wait_probe_kernel<<<1, 32, 0, st>>>(d_status, (unsigned long long)(wait_ms * 1e6));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("dr_selftest_wait_timeout: launch", e);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail("dr_selftest_wait_timeout: synchronize", e);
+  int32_t v = 0;
+  e = cudaMemcpy(&v, d_status, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail("dr_selftest_wait_timeout: read", e);
+  if (v == kDevTmaTimeout) {
+    set_error("bounded wait ran out after %.1f ms (code %d)", wait_ms, v);
+    return DR_ERR_TIMEOUT;
+  }
+  return DR_OK;
+}
+
 // ------------------------------------------- no-allocation entry point ---
 // The rows kernel with its geometry tables in a file-scope device array
 // instead of a plan's cudaMalloc'd block, for callers that may not allocate

@@ -28,7 +28,8 @@ KERNELS = {0: "rows", 1: "pixels", 2: "intervals"}
 # every symbol include/dr.h declares (checked by the CPU tests)
 EXPORTS = ("dr_plan", "dr_plan_destroy", "dr_plan_get_info", "dr_plan_device_bytes",
            "dr_reconstruct", "dr_reconstruct_host", "dr_image_differences",
-           "dr_plan_depths", "dr_plan_check", "dr_status_string", "dr_last_error",
+           "dr_plan_depths", "dr_plan_check", "dr_selftest_wait_timeout",
+           "dr_status_string", "dr_last_error",
            "dr_version", "dr_reconstruct_rows_static", "dr_batch_create", "dr_batch_launch",
            "dr_batch_check", "dr_batch_get_info", "dr_batch_destroy", "dr_server_create",
            "dr_server_submit", "dr_server_poll", "dr_server_wait", "dr_server_fetch",
@@ -132,6 +133,7 @@ def lib():
                 "dr_image_differences": ([P, I32, I32, I32, P, P], I32),
                 "dr_plan_depths": ([P, I32, I32, P, P], I32),
                 "dr_plan_check": ([P], I32),
+                "dr_selftest_wait_timeout": ([P, ctypes.c_double, P], I32),
                 "dr_status_string": ([I32], ctypes.c_char_p),
                 "dr_last_error": ([], ctypes.c_char_p),
                 "dr_version": ([], ctypes.c_char_p),
@@ -500,3 +502,13 @@ def select_pixels(activity, threshold, stream=None):
 
 def version():
     return lib().dr_version().decode()
+
+
+def selftest_wait_timeout(wait_ms=20.0, stream=None):
+    """dr_selftest_wait_timeout: run the bounded-wait failure path once.
+    Returns (status code, the device status word)."""
+    import torch
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = lib().dr_selftest_wait_timeout(_dptr(status), float(wait_ms),
+                                         ctypes.c_void_p(_stream_handle(stream)))
+    return st, int(status.item())
