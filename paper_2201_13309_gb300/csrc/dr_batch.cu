@@ -56,6 +56,7 @@ const void *batch_fn() {
 
 extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
                                      const dr_batch_options *opt_in, dr_batch_t **out) {
+  TraceRange trace_("dr_batch_create");
   if (out) *out = nullptr;
   if (!jobs || n < 1 || !out) {
     set_error("dr_batch_create: need at least one job");
@@ -228,6 +229,7 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
 }
 
 extern "C" dr_status dr_batch_launch(dr_batch_t *b, dr_stream_t stream) {
+  TraceRange trace_("dr_batch_launch");
   if (!b) {
     set_error("dr_batch_launch: null batch");
     return DR_ERR_INVALID_ARG;

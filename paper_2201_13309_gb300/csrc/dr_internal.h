@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include <cuda.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
@@ -85,6 +86,15 @@ dr_status launch_plan(const dr_plan_t *p, const uint16_t *img, void *out,
 // Reconstruction launch of a plan (defined with the kernels).
 dr_status launch_reconstruct(const dr_plan_t *p, const uint16_t *img, void *out,
                              struct CUstream_st *st);
+
+// A named range for profilers' timelines (NVTX; nothing happens unless a
+// tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
 
 void set_error(const char *fmt, ...);
 dr_status cuda_fail(const char *what, int err);

@@ -664,6 +664,7 @@ static dr_status plan_parts(bool intervals, const dr_geometry *g, const double *
 extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t K,
                              const double *edges, int32_t B, const dr_plan_options *opt,
                              dr_plan_t **out) {
+  TraceRange trace_("dr_plan");
   if (out) *out = nullptr;
   if (!g || !wires || !edges || !out) {
     set_error("dr_plan: null argument");

@@ -245,6 +245,7 @@ using namespace dr;
 
 extern "C" dr_status dr_reconstruct(const dr_plan_t *p, const uint16_t *img, void *out,
                                     dr_stream_t stream) {
+  TraceRange trace_("dr_reconstruct");
   if (!p) {
     set_error("dr_reconstruct: null plan");
     return DR_ERR_INVALID_ARG;
@@ -270,6 +271,7 @@ extern "C" dr_status dr_reconstruct(const dr_plan_t *p, const uint16_t *img, voi
 
 extern "C" dr_status dr_reconstruct_host(const dr_plan_t *p, const uint16_t *h_img, void *h_out,
                                          uint16_t *d_img, void *d_out, dr_stream_t stream) {
+  TraceRange trace_("dr_reconstruct_host");
   if (!p || !h_img || !h_out || !d_img || !d_out) {
     if (p && (size_t)p->rows * p->cols == 0) return DR_OK;
     set_error("dr_reconstruct_host: null argument");
@@ -291,6 +293,7 @@ extern "C" dr_status dr_reconstruct_host(const dr_plan_t *p, const uint16_t *h_i
 
 extern "C" dr_status dr_image_differences(const uint16_t *img, int32_t K, int32_t rows,
                                           int32_t cols, int32_t *d, dr_stream_t stream) {
+  TraceRange trace_("dr_image_differences");
   if (K < 1 || rows < 0 || cols < 0) {
     set_error("dr_image_differences: bad sizes");
     return DR_ERR_INVALID_ARG;
@@ -311,6 +314,7 @@ extern "C" dr_status dr_image_differences(const uint16_t *img, int32_t K, int32_
 
 extern "C" dr_status dr_plan_depths(const dr_plan_t *p, int32_t r0, int32_t nrows, double *d,
                                     dr_stream_t stream) {
+  TraceRange trace_("dr_plan_depths");
   if (!p || r0 < 0 || nrows < 0 || r0 + nrows > p->rows) {
     set_error("dr_plan_depths: bad arguments");
     return DR_ERR_INVALID_ARG;
@@ -540,6 +544,7 @@ dr_status stream_set(StreamSet **out) {
 extern "C" dr_status dr_reconstruct_streamed(const dr_plan_t *p, const uint16_t *h_img,
                                              void *h_out, void *d_ws, size_t ws_bytes,
                                              int32_t slab_rows, dr_stream_t stream) {
+  TraceRange trace_("dr_reconstruct_streamed");
   if (!p) {
     set_error("dr_reconstruct_streamed: null plan");
     return DR_ERR_INVALID_ARG;
@@ -804,6 +809,7 @@ __global__ void select_write_kernel(const float *__restrict__ act, long long n, 
 
 extern "C" dr_status dr_pixel_activity(const uint16_t *img, int32_t K, int32_t rows, int32_t cols,
                                        float *act, dr_stream_t stream) {
+  TraceRange trace_("dr_pixel_activity");
   const long long P = (long long)rows * cols;
   if (K < 1 || rows < 0 || cols < 0) {
     set_error("dr_pixel_activity: bad sizes");
@@ -842,6 +848,7 @@ extern "C" size_t dr_select_scratch_bytes(int64_t n) {
 extern "C" dr_status dr_select_pixels(const float *act, int64_t n, float threshold,
                                       int32_t *idx, int32_t *count, void *scratch,
                                       size_t scratch_bytes, dr_stream_t stream) {
+  TraceRange trace_("dr_select_pixels");
   if (n < 0 || n > 2147483647LL || !act || !idx || !count || !scratch) {
     set_error("dr_select_pixels: bad arguments");
     return DR_ERR_INVALID_ARG;
@@ -870,6 +877,7 @@ extern "C" dr_status dr_select_pixels(const float *act, int64_t n, float thresho
 extern "C" dr_status dr_reconstruct_selected(const dr_plan_t *p, const uint16_t *img,
                                              const int32_t *idx, int32_t n, void *out,
                                              dr_stream_t stream) {
+  TraceRange trace_("dr_reconstruct_selected");
   if (!p || n < 0) {
     set_error("dr_reconstruct_selected: bad arguments");
     return DR_ERR_INVALID_ARG;

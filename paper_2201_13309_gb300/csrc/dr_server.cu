@@ -275,6 +275,7 @@ void scheduler(dr_server_t *s) {
     std::vector<std::pair<Request *, dr_status>> failed;
     std::vector<dr_plan_t *> dead;
     for (Request *r : admit) {
+      TraceRange trace_("server: plan, upload and launch of one request");
       dr_status st = DR_OK;
       if (!r->pe) {
         dr_plan_t *p = nullptr;
@@ -350,6 +351,7 @@ Request *find(dr_server_t *s, uint64_t id) {
 }  // namespace
 
 extern "C" dr_status dr_server_create(const dr_server_options *o, dr_server_t **out) {
+  TraceRange trace_("dr_server_create");
   if (out) *out = nullptr;
   if (!o || !out || o->budget_bytes < (size_t(1) << 20) || o->slots < 0 || o->slots > 64) {
     set_error("dr_server_create: need options with budget_bytes >= 1 MiB and 0..64 slots");
@@ -404,6 +406,7 @@ extern "C" dr_status dr_server_create(const dr_server_options *o, dr_server_t **
 extern "C" dr_status dr_server_submit(dr_server_t *s, const dr_geometry *g, const double *wires,
                                       int32_t K, const double *edges, int32_t B,
                                       const uint16_t *h_images, uint64_t *id) {
+  TraceRange trace_("dr_server_submit");
   if (!s || !g || !wires || !edges || !id || K < 2 || B < 1 || g->rows < 0 || g->cols < 0) {
     set_error("dr_server_submit: bad arguments");
     return DR_ERR_INVALID_ARG;
@@ -511,6 +514,7 @@ extern "C" dr_status dr_server_fetch(dr_server_t *s, uint64_t id, const void **d
 
 extern "C" dr_status dr_server_fetch_into(dr_server_t *s, uint64_t id, void *dst,
                                           size_t dst_bytes, dr_stream_t stream) {
+  TraceRange trace_("dr_server_fetch_into");
   const void *src = nullptr;
   dr_status st = dr_server_fetch(s, id, &src, nullptr);
   if (st != DR_OK) return st;
