@@ -653,18 +653,20 @@ __global__ void __launch_bounds__(512, 1) batch_rows_kernel(const BatchScan *__r
 //  1. All threads evaluate the tile's K x tile_cols depth positions into
 //     shared memory (thread (pixel, share) takes steps share, share + G, ...)
 //     while the TMA copies the image tile.
-//  2. One warp per slab finds the slab's data span [jlo, jhi): bin j can
-//     hold data for some pixel only if e_{j+1} > min d_0 and e_j < max
-//     d_{K-1}.
-//  3. Every share gets an equal part of the span, which it walks (binary
-//     search of its first step, then bins and steps together), and an equal
-//     part of the bins outside it, which are zero.  The bin loop is uniform
-//     over the warp, so the 32 lanes store bin j as one coalesced line.
+//  2. Every warp finds the data span [jlo, jhi) of its slab (each warp holds
+//     whole slabs): bin j can hold data for some pixel only if
+//     e_{j+1} > min d_0 and e_j < max d_{K-1}.
+//  3. Every share gets an equal part of the span, which it walks (search of
+//     its first step, then bins and steps together), and an equal part of
+//     the bins outside it, which are zero.  The bin loop is uniform over the
+//     warp, so the 32 lanes store bin j as one coalesced line.  The searches
+//     start from a linear guess and are exact (binary search as fallback).
 // A bin is zero for a pixel when e_{j+1} <= d_0 or e_j >= d_{K-1}, the same
 // rule as the rows kernel's, so both kernels give bitwise the same bins.
-// Shared-memory layout: [0, 128) mbarrier and the slab spans, then the image
-// tile [Kpad][tile_cols] uint16, the depth positions [K][tile_cols], the bin
-// edges [B + 1].
+// Shared-memory layout: [0, 128) mbarrier, then the image tile
+// [Kpad][tile_cols] uint16, the depth positions [K][tile_cols], the bin edges
+// [B + 1].
+
 // minimum / maximum over aligned groups of `width` lanes (a power of two
 // <= 32); every lane of the warp takes part
 template <class T>
