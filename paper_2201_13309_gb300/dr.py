@@ -205,7 +205,11 @@ class Plan:
 
     geom: dict with beam_origin, beam_dir, det_origin, row_step, col_step,
     rows, cols, wire_axis, wire_radius (mm); wires [K, 3]; edges [B + 1]
-    (depth, mm, strictly increasing).
+    (depth, mm, strictly increasing).  edge: "leading", "trailing" or
+    "both"; out_dtype "f32" / "bf16"; geom_precision "fp32" / "fp64";
+    tile_cols / bin_groups: launch shape (0 = default); force_pixels /
+    force_intervals: use the per-pixel or the interval kernel instead of the
+    one the plan picks (info()["kernel"] tells which).
     """
 
     def __init__(self, geom, wires, edges, edge="leading", out_dtype="f32",
