@@ -99,3 +99,28 @@ def test_admission_waits_for_memory_and_rejects_oversize():
     with pytest.raises(dr.DrError):
         srv.poll(123456)
     srv.close()
+
+
+def test_served_scans_take_every_kernel():
+    """The server builds its plans with dr_plan, so a rotated detector is
+    served by the per-pixel kernel and a wire that also climbs across the
+    beam by the interval kernel; each result equals dr_reconstruct's."""
+    rot = synth.spot_scan(45, 6, 96, 33, 6, -60.0, 60.0, 1.0, rotate_deg=8.0,
+                          depth_range=(-0.03, 0.03))
+    climb = synth.tiny_scan(46, rows=4, cols=40, K=30, roi_origin=(1900, 1000),
+                            det_rows=2048, det_cols=2048)
+    climb.wires = synth.wire_path(30, dy=0.005)
+    climb.edges = synth.bin_edges(-200.0, -140.0, 1.0)
+    srv = dr.Server(budget_bytes=1 << 28, slots=2)
+    for sc, kernel in ((rot, "pixels"), (climb, "intervals")):
+        plan = dr.Plan(sc.geom, sc.wires, sc.edges)
+        assert plan.info()["kernel"] == kernel
+        h = torch.from_numpy(np.ascontiguousarray(sc.images).view(np.int16)).pin_memory()
+        rid = srv.submit(sc.geom, sc.wires, sc.edges, h)
+        srv.wait(rid, timeout=60)
+        got = _result(srv, rid, sc)
+        srv.release(rid)
+        ref = plan.reconstruct(h.cuda())
+        torch.cuda.synchronize()
+        assert torch.equal(ref.view(torch.int32), got.view(torch.int32))
+    srv.close()
