@@ -288,6 +288,13 @@ dr_status dr_batch_check(dr_batch_t *batch);
 dr_status dr_batch_get_info(const dr_batch_t *batch, dr_batch_info *info);
 void dr_batch_destroy(dr_batch_t *batch);
 
+/* One-shot form: dr_batch_create, dr_batch_launch on stream, wait for the
+ * stream, dr_batch_check, dr_batch_destroy.  For a set of scans reconstructed
+ * once; a set replayed many times should keep its batch (graph capture and
+ * tables are built at creation).  Synchronizes the stream and the device. */
+dr_status dr_batch_reconstruct(const dr_job *jobs, int32_t n, const dr_batch_options *options,
+                               dr_stream_t stream);
+
 /* ---- Serving: a stream of requests ----------------------------------------
  * A server takes reconstruction requests of any ROI, step and bin count as
  * they arrive and runs them concurrently on one GPU (the paper's Sec. II names

@@ -272,3 +272,18 @@ extern "C" dr_status dr_batch_get_info(const dr_batch_t *b, dr_batch_info *info)
 }
 
 extern "C" void dr_batch_destroy(dr_batch_t *b) { destroy(b); }
+
+extern "C" dr_status dr_batch_reconstruct(const dr_job *jobs, int32_t n,
+                                          const dr_batch_options *options, dr_stream_t stream) {
+  TraceRange trace_("dr_batch_reconstruct");
+  dr_batch_t *b = nullptr;
+  dr_status st = dr_batch_create(jobs, n, options, &b);
+  if (st != DR_OK) return st;
+  st = dr_batch_launch(b, stream);
+  if (st == DR_OK) {
+    const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    st = e == cudaSuccess ? dr_batch_check(b) : cuda_fail("dr_batch_reconstruct", e);
+  }
+  destroy(b);
+  return st;
+}

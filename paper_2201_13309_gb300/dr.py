@@ -31,7 +31,8 @@ EXPORTS = ("dr_plan", "dr_plan_destroy", "dr_plan_get_info", "dr_plan_device_byt
            "dr_plan_depths", "dr_plan_check", "dr_selftest_wait_timeout",
            "dr_status_string", "dr_last_error",
            "dr_version", "dr_reconstruct_rows_static", "dr_batch_create", "dr_batch_launch",
-           "dr_batch_check", "dr_batch_get_info", "dr_batch_destroy", "dr_server_create",
+           "dr_batch_check", "dr_batch_get_info", "dr_batch_destroy", "dr_batch_reconstruct",
+           "dr_server_create",
            "dr_server_submit", "dr_server_poll", "dr_server_wait", "dr_server_fetch",
            "dr_server_fetch_into", "dr_server_release", "dr_server_get_stats",
            "dr_server_destroy", "dr_reconstruct_streamed", "dr_pixel_activity",
@@ -145,6 +146,8 @@ def lib():
                 "dr_batch_check": ([P], I32),
                 "dr_batch_get_info": ([P, ctypes.POINTER(BatchInfo)], I32),
                 "dr_batch_destroy": ([P], None),
+                "dr_batch_reconstruct": ([ctypes.POINTER(Job), I32, ctypes.POINTER(BatchOptions),
+                                          P], I32),
                 "dr_server_create": ([ctypes.POINTER(ServerOptions), ctypes.POINTER(P)], I32),
                 "dr_server_submit": ([P, ctypes.POINTER(Geometry), P, I32, P, I32, P,
                                       ctypes.POINTER(ctypes.c_uint64)], I32),
@@ -335,6 +338,32 @@ class Plan:
             pass
 
 
+def _jobs_array(jobs):
+    arr = (Job * len(jobs))()
+    for i, (plan, images, out) in enumerate(jobs):
+        plan._check_shapes(images, out)
+        arr[i].plan = plan.handle
+        arr[i].d_images = images.data_ptr()
+        arr[i].d_out = out.data_ptr()
+    return arr
+
+
+def _batch_options(ctas_per_sm=0, max_tile_cols=0, threads=0):
+    o = BatchOptions()
+    o.ctas_per_sm = int(ctas_per_sm)
+    o.max_tile_cols = int(max_tile_cols)
+    o.threads = int(threads)
+    return o
+
+
+def batch_reconstruct(jobs, stream=None, **options):
+    """dr_batch_reconstruct: the (plan, images, out) jobs in one persistent
+    launch, built, run, waited for and released in one call."""
+    arr = _jobs_array(jobs)
+    check(lib().dr_batch_reconstruct(arr, len(jobs), ctypes.byref(_batch_options(**options)),
+                                     ctypes.c_void_p(_stream_handle(stream))))
+
+
 class Batch:
     """dr_batch: several (plan, images, out) jobs reconstructed by one
     persistent launch replayed from a CUDA graph.  The tensors are bound at
@@ -343,16 +372,8 @@ class Batch:
     def __init__(self, jobs, ctas_per_sm=0, max_tile_cols=0, threads=0):
         self._keep = list(jobs)
         self.ctas_per_sm = ctas_per_sm
-        arr = (Job * len(jobs))()
-        for i, (plan, images, out) in enumerate(jobs):
-            plan._check_shapes(images, out)
-            arr[i].plan = plan.handle
-            arr[i].d_images = images.data_ptr()
-            arr[i].d_out = out.data_ptr()
-        o = BatchOptions()
-        o.ctas_per_sm = int(ctas_per_sm)
-        o.max_tile_cols = int(max_tile_cols)
-        o.threads = int(threads)
+        arr = _jobs_array(jobs)
+        o = _batch_options(ctas_per_sm, max_tile_cols, threads)
         h = ctypes.c_void_p()
         check(lib().dr_batch_create(arr, len(jobs), ctypes.byref(o), ctypes.byref(h)))
         self._h = h

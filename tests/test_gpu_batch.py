@@ -60,6 +60,20 @@ def test_batch_matches_per_scan_launches_bitwise():
     assert np.all(np.abs(got - want) <= 1e-4 * s)
 
 
+def test_one_shot_batch_reconstruct():
+    """dr_batch_reconstruct (create, launch, wait, check, destroy in one call)
+    gives the per-scan results bitwise."""
+    jobs, refs = [], []
+    for sc, edge in _scans():
+        plan = dr.Plan(sc.geom, sc.wires, sc.edges, edge=edge)
+        img = _dev(sc.images)
+        refs.append(plan.reconstruct(img))
+        jobs.append((plan, img, torch.full_like(refs[-1], float("nan"))))
+    dr.batch_reconstruct(jobs)
+    for (_, _, out), ref in zip(jobs, refs):
+        assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
+
+
 @pytest.mark.parametrize("per_sm,cap,nt", [(2, 0, 512), (2, 64, 512), (1, 32, 512), (1, 0, 256),
                                            (2, 0, 256)])
 def test_batch_modes_agree(per_sm, cap, nt):
