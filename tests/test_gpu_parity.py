@@ -340,6 +340,32 @@ def test_deterministic_and_stream_async():
     assert torch.equal(a.view(torch.int32), b.view(torch.int32))
 
 
+@pytest.mark.parametrize("kw", [{}, {"force_pixels": True}, {"force_intervals": True}])
+def test_one_plan_on_two_streams_at_once(kw):
+    """A plan is read-only after creation: the same plan on two streams with
+    different images gives each stream's result bitwise as run alone."""
+    sc = synth.tiny_scan(14, rows=24, cols=128, K=41)
+    other = synth.tiny_scan(15, rows=24, cols=128, K=41).images
+    plan = dr.Plan(sc.geom, sc.wires, sc.edges, **kw)
+    a_img, b_img = to_dev(sc.images), to_dev(other)
+    a_ref, b_ref = plan.reconstruct(a_img), plan.reconstruct(b_img)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for _ in range(3):
+        a_out, b_out = torch.empty_like(a_ref), torch.empty_like(b_ref)
+        with torch.cuda.stream(s1):
+            plan.reconstruct(a_img, a_out, stream=s1)
+        with torch.cuda.stream(s2):
+            plan.reconstruct(b_img, b_out, stream=s2)
+        outs.append((a_out, b_out))
+    torch.cuda.synchronize()
+    plan.check_device()
+    for a_out, b_out in outs:
+        assert torch.equal(a_out.view(torch.int32), a_ref.view(torch.int32))
+        assert torch.equal(b_out.view(torch.int32), b_ref.view(torch.int32))
+
+
 def test_end_to_end_host_buffers():
     sc = synth.tiny_scan(12)
     plan = dr.Plan(sc.geom, sc.wires, sc.edges)
