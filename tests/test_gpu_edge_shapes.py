@@ -81,3 +81,38 @@ def test_empty_roi(kernel, kw):
                                      device="cuda"), out)
         torch.cuda.synchronize()
         plan.check_device()
+
+
+def uneven_edges(seed, lo_um, hi_um):
+    """Bin edges with widths drawn from 0.2 to 3 um: the kernels' edge
+    searches start from a uniform-bin guess and must fall back to a binary
+    search here."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = rng.uniform(0.2, 3.0, 400)
+    e = lo_um + np.concatenate([[0.0], np.cumsum(w)])
+    return e[e <= hi_um] * 1e-3
+
+
+@pytest.mark.parametrize("kernel,kw", KERNELS, ids=[k for k, _ in KERNELS])
+def test_uneven_bins(kernel, kw):
+    sc = synth.tiny_scan(94, rows=6, cols=48, K=41)
+    sc.edges = uneven_edges(94, -20.0, 70.0)
+    assert np.ptp(np.diff(sc.edges)) > 2e-3
+    check(sc, kernel, kw)
+
+
+def test_uneven_bins_rows_and_pixels_bitwise():
+    sc = synth.tiny_scan(95, rows=6, cols=64, K=41)
+    sc.edges = uneven_edges(95, -20.0, 70.0)
+    img = torch.from_numpy(np.ascontiguousarray(sc.images).view(np.int16)).cuda()
+    a = dr.Plan(sc.geom, sc.wires, sc.edges).reconstruct(img)
+    b = dr.Plan(sc.geom, sc.wires, sc.edges, force_pixels=True).reconstruct(img)
+    torch.cuda.synchronize()
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+
+
+def test_uneven_bins_rotated():
+    sc = synth.spot_scan(96, 4, 72, 33, 8, -60.0, 60.0, 1.0, rotate_deg=9.0,
+                         depth_range=(-0.03, 0.03))
+    sc.edges = uneven_edges(96, -70.0, 70.0)
+    check(sc, "pixels", {})
