@@ -305,6 +305,25 @@ def test_gpu_depths_vs_oracle():
     assert np.abs(d32 - ref).max() < 4.0 * 2.0 ** -p32.info()["fixed_shift"] + 1e-10
 
 
+def test_gpu_depths_per_pixel_and_interval_plans():
+    """dr_plan_depths for constants held per pixel (rotated detector) and for
+    an interval plan (a wire climbing across the beam, travelling backwards),
+    in the original step order."""
+    rot = synth.spot_scan(3, 6, 40, 21, 4, -50, 50, 1.0, rotate_deg=7.0, tilt_deg=2.0)
+    climb = synth.tiny_scan(4, rows=4, cols=24, K=30, roi_origin=(1900, 1000),
+                            det_rows=2048, det_cols=2048)
+    climb.wires = synth.wire_path(30, dy=0.005)[::-1].copy()
+    # a wire moving across the beam (eta != 0) makes the FP32 remainder
+    # ~eta * Z / D (0.05 mm here), taken with an approximate reciprocal of
+    # D - eta: a few pm of error (measured 8.6 pm), 1e-5 of a 1 um step
+    for sc, kernel, extra in ((rot, "pixels", 0.0), (climb, "intervals", 2e-8)):
+        plan = dr.Plan(sc.geom, sc.wires, sc.edges)
+        assert plan.info()["kernel"] == kernel
+        ref = O.depths(sc.geom, sc.wires)
+        got = plan.depths().cpu().numpy()
+        assert np.abs(got - ref).max() < 4.0 * 2.0 ** -plan.info()["fixed_shift"] + 1e-10 + extra
+
+
 def test_extreme_counts_and_constant_pixels():
     sc = synth.tiny_scan(10, rows=4, cols=64, K=17)
     im = sc.images.copy()
