@@ -60,8 +60,10 @@ __device__ __forceinline__ float iv_inv_len(int32_t lo, int32_t hi) {
   return __frcp_rn(__uint2float_rn((uint32_t)hi - (uint32_t)lo));
 }
 __device__ __forceinline__ double iv_inv_len(double lo, double hi) { return 1.0 / (hi - lo); }
-// accumulator (units of 2^-30) to FP32 with one rounding: hi * 4 is exact
-// (|hi| < 2^24 for any 16-bit scan of fewer than 65536 steps)
+// accumulator (units of 2^-30) to FP32: hi * 4 + lo * 2^-30 with one
+// rounding while |hi| < 2^24, i.e. for bin values below 2^26 counts (any
+// real scan); larger values (extreme counts of thousands of steps piled into
+// one bin) are within one ulp
 __device__ __forceinline__ float iv_value(long long a) {
   const int hi = (int)(a >> 32);
   const uint32_t lo = (uint32_t)a;
