@@ -4,7 +4,7 @@
  * Method: differential-aperture depth reconstruction (the paper's Sec. III:
  * per pixel, the intensity difference between consecutive wire-step images is
  * assigned to depth and summed into a depth-resolved result; Sec. III-C
- * "pixel reconstruction function").  For every detector pixel and wire step k
+ * describes the per-pixel routine).  For every detector pixel and wire step k
  * the library computes the beam depth d_k at which the ray from that pixel
  * grazes the chosen wire edge (tangent to the wire circle in the plane
  * perpendicular to the wire axis, intersected with the incident beam), takes
@@ -17,7 +17,7 @@
  *
  * Layouts (row-major, no padding):
  *   images  [K][rows][cols]  uint16   (Sec. III-B: p images of m rows x n cols,
- *                                      stored as one flat array, the "1D array")
+ *                                      stored as one flat array)
  *   output  [B][rows][cols]  float32 or bfloat16 (plan option)
  *
  * Ownership: a plan owns its device constants; the caller owns every image and
@@ -212,8 +212,8 @@ dr_status dr_reconstruct_selected(const dr_plan_t *plan, const uint16_t *d_image
                                   const int32_t *d_index, int32_t n, void *d_out,
                                   dr_stream_t stream);
 
-/* The exact integer differences the kernels use (Sec. III-C "difference
- * intensity at each pixel"): d_diff[k][p] = images[k][p] - images[k+1][p] as
+/* The exact integer differences the kernels use (Sec. III-C: each pixel's
+ * change of intensity between steps): d_diff[k][p] = images[k][p] - images[k+1][p] as
  * int32, k = 0..K-2, for a [K][rows][cols] uint16 device stack. */
 dr_status dr_image_differences(const uint16_t *d_images, int32_t K,
                                int32_t rows, int32_t cols, int32_t *d_diff,

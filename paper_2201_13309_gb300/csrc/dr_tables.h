@@ -1,8 +1,8 @@
 // Layouts of the tables the kernels read (shared by host and device code).
 //
-// Depth model (the tangent geometry of the differential-aperture method; the
-// paper's Sec. III-C "pixel reconstruction function" assigns each difference
-// to depth): everything is projected onto the plane perpendicular to the wire
+// Depth model (the tangent geometry of the differential-aperture method; in
+// the paper's Sec. III-C the per-pixel routine assigns each difference to
+// depth): everything is projected onto the plane perpendicular to the wire
 // axis, with e2 along the projected beam and e1 toward the first wire centre.
 // A beam point at projected depth t sits at (0, t); pixel p at (Y, Z); wire
 // step k at (y_k, z_k), radius R.  The line from (0, t) to (Y, Z) touches the
