@@ -242,6 +242,29 @@ def dist_setup():
     return world, rank, local
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the
+    machine type)."""
+    import platform
+    import subprocess
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine() or "unknown"
+
+
 def cpu_oracle_sample(spec, host_rows, rows_idx, threads, budget_s=None):
     """Time the FP64 oracle on the given rows (one-row geometries)."""
     from oracle import oracle as O
@@ -261,7 +284,7 @@ def cpu_oracle_sample(spec, host_rows, rows_idx, threads, budget_s=None):
 def synth_rows_host(spec, rows_idx, seed=0):
     """uint16 [K, 1, W] stacks of the chosen rows, generated on the host with
     the same forward model as the device scan (spots + Poisson background)."""
-    from paper_2201_13309_gb300 import synth
+    from tests.gen import synth
 
     rng = np.random.Generator(np.random.PCG64(seed + 12345))
     idx, val = synth.spot_contributions(spec.geom, spec.wires, spec.scat)
@@ -283,7 +306,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return 0
     from oracle import oracle as O
-    from paper_2201_13309_gb300 import synth
+    from tests.gen import synth
 
     O.build()
     spec = synth.full_scan_spec(0)
@@ -310,7 +333,7 @@ def run_reference(args, world, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": sample},
+                         "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -412,7 +435,7 @@ def batch_waves(specs, budget_bytes):
 def small_roi_spec(seed):
     """A scan of the uneven-batch distribution restricted to small ROIs
     (256^2 or 512^2), where launch tails dominate a per-scan loop."""
-    from paper_2201_13309_gb300 import synth
+    from tests.gen import synth
 
     for s in range(seed * 1000, seed * 1000 + 1000):
         sp = synth.batch_scan_spec(s)
@@ -426,7 +449,8 @@ def run_batched(args, dev, specs=None):
     (replayed from a captured CUDA graph), same plans, same buffers."""
     import torch
 
-    from paper_2201_13309_gb300 import autotune, dr, synth
+    from paper_2201_13309_gb300 import autotune, dr
+    from tests.gen import synth
 
     if specs is None:
         specs = [synth.batch_scan_spec(s) for s in range(args.batch_scans)]
@@ -518,7 +542,8 @@ def run_served(args, dev):
 
     import torch
 
-    from paper_2201_13309_gb300 import dr, synth
+    from paper_2201_13309_gb300 import dr
+    from tests.gen import synth
 
     pool, up_gbs = [], []
     placement = near_gpu(dev)
@@ -743,7 +768,8 @@ def main():
     import torch
 
     import __graft_entry__
-    from paper_2201_13309_gb300 import dr, synth
+    from paper_2201_13309_gb300 import dr
+    from tests.gen import synth
 
     if world > 1:
         import torch.distributed as tdist
@@ -912,7 +938,7 @@ def main():
         host = synth_rows_host(spec, rows_idx)
         dt = cpu_oracle_sample(spec, host, rows_idx, threads)
         cpu = {"value": len(rows_idx) * spec.geom["cols"] * spec.K / dt, "unit": UNIT,
-               "cores": threads, "kind": "oracle",
+               "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
                "sample": (f"{len(rows_idx)} of 2048 detector rows ({len(rows_idx) * 2048} pixels "
                           f"x 401 steps x 1001 bins), FP64, {threads} threads, {dt:.1f} s")}
 

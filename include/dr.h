@@ -154,7 +154,10 @@ void dr_plan_destroy(dr_plan_t *plan);
 dr_status dr_plan_get_info(const dr_plan_t *plan, dr_plan_info *info);
 size_t dr_plan_device_bytes(const dr_plan_t *plan);
 
-/* Reconstruct one scan: d_images [K][rows][cols] uint16 in device memory,
+/* Reconstruct one scan (the per-pixel routine of Sec. III-C, for every pixel
+ * of the ROI: exact differences between consecutive wire-step images, each
+ * spread over the depth bins its wire-edge interval overlaps, Sec. III-A):
+ * d_images [K][rows][cols] uint16 in device memory,
  * d_out [B][rows][cols] (float or bf16 per the plan) in device memory.  Every
  * output element is written exactly once (no prior clearing needed).  Allocates
  * nothing; asynchronous on stream.  A plan may be used from several streams at
@@ -376,15 +379,23 @@ void dr_server_destroy(dr_server_t *server);
  * do not run along the wire axis DR_ERR_UNSUPPORTED.  Arguments are those of
  * dr_plan + dr_reconstruct; d_status is an optional device int32 that is
  * cleared and then receives a device-side error code (nonzero: a bounded wait
- * ran out); with d_status null the code stays in the library's array.
+ * ran out).  With d_status null no error is reported: the code goes to a
+ * word in the library's array that nothing reads and the next call clears,
+ * so pass a status word wherever a timeout must be seen.  The library cannot
+ * see buffer sizes: d_images and d_out must hold the full [K][rows][cols] and
+ * [B][rows][cols] arrays (the Python binding checks this).
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Each call copies its tables into the array on
- * stream (the host side is serialised by a lock), so every call shares the
- * array and leaves its own tables there: calls on one stream are ordered,
- * but calls whose work overlaps on the GPU (other streams, other threads)
- * race on the array and must not be issued. */
+ * before any stream capture.  Each call writes its tables into a host
+ * buffer inside the library and copies them into the array with an
+ * asynchronous copy from that (pageable) buffer on stream: the copy first
+ * waits for the work already queued on stream, and the call returns once
+ * the bytes are staged, so the host buffer is reused by the next call.  A
+ * lock serialises the calls' host side.  Every call shares the array and
+ * leaves its own tables there: calls on one stream are ordered, but calls
+ * whose work overlaps on the GPU (other streams, other threads) race on the
+ * array and must not be issued. */
 #define DR_STATIC_SCRATCH_BYTES (2u << 20)
 dr_status dr_reconstruct_rows_static(const dr_geometry *geometry,
                                      const double *wire_centres, int32_t K,

@@ -21,8 +21,6 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
-# tests/test_oracle_mutants.py points this at deliberately broken builds
-_ALT_LIB = os.environ.get("DR_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
 
@@ -50,11 +48,8 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            if _ALT_LIB:
-                lib = ctypes.CDLL(_ALT_LIB)
-            else:
-                build()
-                lib = ctypes.CDLL(_LIB_PATH)
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
             P = ctypes.c_void_p
             i32 = ctypes.c_int
             lib.oracle_depths.argtypes = [P, i32, P, i32, i32, i32, i32, P]

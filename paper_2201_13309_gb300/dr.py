@@ -486,10 +486,37 @@ def reconstruct_rows_static(geom, wires, edges, images, out, status=None, edge="
     """dr_reconstruct_rows_static: the rows kernel with no allocation at all.
 
     images: CUDA [K, rows, cols] 16-bit; out: CUDA float32 [B, rows, cols]
-    (caller-allocated); status: optional CUDA int32 tensor of one element.
+    (caller-allocated); status: optional CUDA int32 tensor of one element
+    (with None, a device-side error code is not reported).  The C entry
+    point cannot see buffer sizes, so every shape, type, layout and device is
+    checked here before the call (ValueError).
     """
+    import torch
     w = np.ascontiguousarray(wires, dtype=np.float64)
     e = np.ascontiguousarray(edges, dtype=np.float64)
+    if w.ndim != 2 or w.shape[1] != 3:
+        raise ValueError(f"wires must be [K, 3], got {w.shape}")
+    if e.ndim != 1 or e.shape[0] < 2:
+        raise ValueError(f"edges must be [B + 1] with B >= 1, got {e.shape}")
+    K, B = int(w.shape[0]), int(e.shape[0] - 1)
+    H, W = int(geom["rows"]), int(geom["cols"])
+    if H * W > 0:
+        if images is None or out is None:
+            raise ValueError("images and out are required for a non-empty ROI")
+        if tuple(images.shape) != (K, H, W):
+            raise ValueError(f"images {tuple(images.shape)} != {(K, H, W)}")
+        if images.element_size() != 2 or images.is_floating_point() or not images.is_contiguous():
+            raise ValueError("images must be a contiguous 16-bit integer tensor")
+        if tuple(out.shape) != (B, H, W):
+            raise ValueError(f"out {tuple(out.shape)} != {(B, H, W)}")
+        if out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float32 tensor")
+    if status is not None and (status.dtype != torch.int32 or status.numel() != 1):
+        raise ValueError("status must be a one-element int32 tensor")
+    on_device = [status] + ([images, out] if H * W > 0 else [])
+    for t in on_device:
+        if t is not None and (not t.is_cuda or t.device.index != torch.cuda.current_device()):
+            raise ValueError("images, out and status must be on the current CUDA device")
     g = geometry_struct(geom, edge)
     check(lib().dr_reconstruct_rows_static(
         ctypes.byref(g), w.ctypes.data_as(ctypes.c_void_p), w.shape[0],

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 from oracle import oracle as O  # noqa: E402
-from paper_2201_13309_gb300 import synth as S  # noqa: E402
+from tests.gen import synth as S  # noqa: E402
 
 
 def odd_case():

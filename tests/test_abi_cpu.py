@@ -7,7 +7,8 @@ import re
 import numpy as np
 import pytest
 
-from paper_2201_13309_gb300 import _build, dr, synth
+from paper_2201_13309_gb300 import _build, dr
+from tests.gen import synth
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -85,3 +86,34 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(dr, "_lib", None)
     with pytest.raises(ImportError):
         dr.lib()
+
+
+def test_static_entry_binding_checks_buffers_before_any_call(monkeypatch):
+    """The no-allocation entry point cannot see buffer sizes; the binding
+    refuses a wrong shape, type or device before it reaches the library."""
+    import torch
+
+    def no_call():
+        raise AssertionError("the library was called")
+
+    monkeypatch.setattr(dr, "lib", no_call)
+    sc = synth.tiny_scan(3, rows=4, cols=8, K=5)
+    K, H, W, B = sc.K, 4, 8, sc.B
+    img = torch.zeros((K, H, W), dtype=torch.int16)
+    good_out = torch.zeros((B, H, W), dtype=torch.float32)
+    cases = [
+        (sc.wires.reshape(-1), sc.edges, img, good_out),              # wires not [K, 3]
+        (sc.wires, sc.edges[:, None], img, good_out),                 # edges not 1-D
+        (sc.wires, sc.edges, img, torch.zeros((B, H, W - 1))),        # out too small
+        (sc.wires, sc.edges, img, torch.zeros((B, H, W), dtype=torch.float64)),
+        (sc.wires, sc.edges, torch.zeros((K, H, W), dtype=torch.int32), good_out),
+        (sc.wires, sc.edges, img[:, :, ::2], torch.zeros((B, H, 4))),  # wrong shape
+        (sc.wires, sc.edges, None, good_out),
+        (sc.wires, sc.edges, img, good_out),                          # host tensors
+    ]
+    for wires, edges, images, out in cases:
+        with pytest.raises(ValueError):
+            dr.reconstruct_rows_static(sc.geom, wires, edges, images, out)
+    with pytest.raises(ValueError):
+        dr.reconstruct_rows_static(sc.geom, sc.wires, sc.edges, img, good_out,
+                                   status=torch.zeros(2, dtype=torch.int32))

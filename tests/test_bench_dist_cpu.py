@@ -66,7 +66,7 @@ def test_reference_arm_other_ranks_do_no_work():
 
 def test_batch_wave_packing():
     import bench
-    from paper_2201_13309_gb300 import synth
+    from tests.gen import synth
 
     specs = [synth.batch_scan_spec(s) for s in range(64)]
     waves = bench.batch_waves(specs, 120e9)

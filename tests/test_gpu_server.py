@@ -6,7 +6,8 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from paper_2201_13309_gb300 import dr, synth  # noqa: E402
+from paper_2201_13309_gb300 import dr  # noqa: E402
+from tests.gen import synth  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from paper_2201_13309_gb300 import synth as S
+from tests.gen import synth as S
 
 R = S.WIRE_R_MM
 YW = S.WIRE_Y_MM
@@ -307,3 +307,72 @@ def test_tiny_scan_peaks_at_scatterer_depths():
             assert abs(mass - W * A) < 5 * sigma + 0.05 * W * A
             checked += 1
     assert checked >= 15
+
+
+def test_trailing_edge_conservation_tiny_scan():
+    """The trailing edge reveals what the leading edge hid: its differences
+    are I_{k+1} - I_k, so wherever a pixel's whole trailing-edge sweep lies
+    inside the bins, the bins sum to I_last - I_first."""
+    sc = S.tiny_scan(0)
+    d = O.depths(sc.geom, sc.wires, "trailing")
+    rows = _inside_rows(sc, d)
+    assert len(rows) > 20
+    out = O.reconstruct(sc.geom, sc.wires, sc.images, sc.edges, edge="trailing")
+    tot = out.sum(0)
+    exp = sc.images[-1].astype(np.int64) - sc.images[0].astype(np.int64)
+    sabs = np.abs(np.diff(sc.images.astype(np.int64), axis=0)).sum(0)
+    err = np.abs(tot[rows] - exp[rows]) / np.maximum(sabs[rows], 1)
+    assert err.max() < 1e-12
+    assert np.abs(exp[rows]).max() > 100          # the sums are not all zero
+
+
+def test_noise_free_scatterer_revealed_by_trailing_edge():
+    """Forward model with one scatterer that starts hidden (between the two
+    tangents at step 0), no noise: the trailing edge uncovers it between the
+    brute-force steps k-1 (hidden) and k (visible).  The trailing-edge
+    reconstruction must put exactly +A on the trailing interval
+    [d_{k-1}, d_k], which contains the scatterer depth, and nothing
+    elsewhere."""
+    geom = S.detector_geometry(3, 2, roi_origin=(30, 0), det_rows=64, det_cols=64)
+    wires = S.wire_path(41)
+    e = S.bin_edges(-50, 50, 1.0)
+    A = 1000.0
+    d = O.depths(geom, wires, "trailing")
+    for s in (-0.0351, -0.0254, -0.0187, -0.0109):
+        scat = S.Scatterers(np.array([s]), np.array([A]))
+        images = np.rint(S.expected_counts(geom, wires, scat)).astype(np.uint16)
+        out = O.reconstruct(geom, wires, images, e, edge="trailing")
+        for r in range(3):
+            vis = images[:, r, 0] > 0
+            kr = int(np.argmax(vis))                 # first visible step
+            assert kr > 0 and not vis[:kr].any() and vis[kr:].all()
+            lo, hi = d[r, 0, kr - 1], d[r, 0, kr]
+            assert lo <= s <= hi
+            jlo = int(np.searchsorted(e, lo, "right") - 1)
+            jhi = int(np.searchsorted(e, hi, "right") - 1)
+            col = out[:, r, 0]
+            band = col[jlo:jhi + 1]
+            assert band.sum() == pytest.approx(A, abs=1e-9)
+            assert (band >= 0).all() and band.max() > 0.4 * A
+            assert np.abs(col).sum() == pytest.approx(A, abs=1e-9)
+
+
+def test_both_edges_hand_computed():
+    """One pixel far along y, three wire steps: the leading edge sits at
+    z_k + R and the trailing edge at z_k - R (the far-detector limit).  With
+    I = (100, 70, 60) the leading differences are +30, +10 and the trailing
+    ones -30, -10; each interval is 1 um long and straddles two 1 um bins
+    half and half.  The both-edge result is the mean of the two."""
+    g = _single_pixel_geom(0.0, 1e9, 0.0)
+    w = np.array([[0.0, YW, 0.0], [0.0, YW, 0.001], [0.0, YW, 0.002]])
+    images = np.array([100, 70, 60], dtype=np.uint16).reshape(3, 1, 1)
+    e = np.array([-26.5, -25.5, -24.5, -23.5, 25.5, 26.5, 27.5, 28.5]) * 1e-3
+    lead = np.array([0, 0, 0, 0, 15, 20, 5], float)
+    trail = np.array([-15, -20, -5, 0, 0, 0, 0], float)
+    got_l = O.reconstruct(g, w, images, e, "leading")[:, 0, 0]
+    got_t = O.reconstruct(g, w, images, e, "trailing")[:, 0, 0]
+    got_b = O.reconstruct(g, w, images, e, "both")[:, 0, 0]
+    tol = 1e-4                 # depths within 1e-9 mm of z +- R: 1e-6 of a bin
+    assert np.abs(got_l - lead).max() < tol
+    assert np.abs(got_t - trail).max() < tol
+    assert np.abs(got_b - 0.5 * (lead + trail)).max() < tol

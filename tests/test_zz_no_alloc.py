@@ -3,18 +3,22 @@
 dr_reconstruct_rows_static serves callers that cannot call cudaMalloc (their
 device memory belongs to another allocator, or their pipeline may not
 allocate while running).  It keeps its geometry tables in a fixed device
-array inside the library, so its results must match the plan-based entry
-point (dr_plan + dr_reconstruct) within the parity tolerance of the other
-GPU tests, call after call, even though each call overwrites the array.
-This file is collected last so a run that stops at the first failure has
-already run every other test.
+array inside the library.  Its results must match the FP64 oracle within the
+parity tolerance of the other GPU tests, and the plan-based entry point
+(dr_plan + dr_reconstruct) within the same tolerance, call after call, even
+though each call overwrites the array.  This file is collected last so a run
+that stops at the first failure has already run every other test.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
-from paper_2201_13309_gb300 import dr, synth  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+from paper_2201_13309_gb300 import dr  # noqa: E402
+from tests.gen import synth  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 FP32_TOL = 1e-4
@@ -40,9 +44,13 @@ def _check_close(got, ref, images):
     assert np.all(got[np.broadcast_to(s == 0, got.shape)] == 0)
 
 
-def test_static_entry_matches_plan_entry_on_two_calls_in_a_row():
+def _oracle(scan, r0=0, nrows=None):
+    return O.reconstruct(scan.geom, scan.wires, scan.images, scan.edges, r0=r0, nrows=nrows)
+
+
+def test_static_entry_matches_oracle_and_plan_entry_on_two_calls_in_a_row():
     a = synth.tiny_scan(21)                                  # 64x64, K=41, B=101
-    b = synth.tiny_scan(22, rows=24, cols=200, K=77)         # other sizes, ragged tile
+    b = synth.tiny_scan(22, rows=24, cols=203, K=77)         # one pixel per thread, ragged tile
     b.edges = synth.bin_edges(-20.0, 90.0, 0.5)
     b_back = synth.Scan(b.geom, b.wires[::-1].copy(), b.edges, b.images[::-1].copy())
     status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
@@ -54,23 +62,56 @@ def test_static_entry_matches_plan_entry_on_two_calls_in_a_row():
         dr.reconstruct_rows_static(scan.geom, scan.wires, scan.edges, img, out, status)
         torch.cuda.synchronize()
         assert int(status.item()) == 0
-        _check_close(out.cpu().numpy(), ref.cpu().numpy(), scan.images)
-    # the same scan again after the other one overwrote the device tables
-    out = torch.empty((a.B, 64, 64), device="cuda")
-    dr.reconstruct_rows_static(a.geom, a.wires, a.edges, _dev(a.images), out)
-    ref = dr.Plan(a.geom, a.wires, a.edges).reconstruct(_dev(a.images))
+        got = out.cpu().numpy()
+        _check_close(got, _oracle(scan), scan.images)
+        _check_close(got, ref.cpu().numpy(), scan.images)
+    # the first scan again, with no status word, after the second one
+    # overwrote the device tables
+    out = torch.full((a.B, 64, 64), float("nan"), device="cuda")
+    dr.reconstruct_rows_static(a.geom, a.wires, a.edges, _dev(a.images), out, status=None)
     torch.cuda.synchronize()
-    _check_close(out.cpu().numpy(), ref.cpu().numpy(), a.images)
+    _check_close(out.cpu().numpy(), _oracle(a), a.images)
+
+
+def test_static_entry_tables_just_under_the_limit():
+    """65480 rows of 6 pixels: 32 B of row constants per row bring the tables
+    to within 256 bytes of the 2 MiB array."""
+    H, W, K = 65480, 6, 41
+    geom = synth.detector_geometry(H, W)
+    geom["row_step"] = [0.0, 0.0, 0.003]
+    geom["det_origin"] = [-(W - 1) / 2 * synth.PITCH_MM, synth.DET_Y_MM, -(H - 1) / 2 * 0.003]
+    wires = synth.wire_path(K)
+    edges = synth.bin_edges(-50.0, 50.0, 1.0)
+    rng = np.random.Generator(np.random.PCG64(5))
+    images = rng.integers(0, 4000, size=(K, H, W), dtype=np.uint16)
+    scan = synth.Scan(geom, wires, edges, images)
+    out = torch.full((scan.B, H, W), float("nan"), device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    dr.reconstruct_rows_static(geom, wires, edges, _dev(images), out, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    got = out.cpu().numpy()
+    for r0 in (0, H // 2, H - 40):
+        _check_close(got[:, r0:r0 + 40], _oracle(scan, r0, 40), images[:, r0:r0 + 40])
+    ref = dr.Plan(geom, wires, edges).reconstruct(_dev(images))
+    _check_close(got, ref.cpu().numpy(), images)
+
+
+def _call_c(geom, wires, edges):
+    """The C entry point itself, with null buffers (it must reject the
+    request before it looks at them)."""
+    w = np.ascontiguousarray(wires, dtype=np.float64)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    g = dr.geometry_struct(geom)
+    return dr.lib().dr_reconstruct_rows_static(
+        ctypes.byref(g), w.ctypes.data_as(ctypes.c_void_p), w.shape[0],
+        e.ctypes.data_as(ctypes.c_void_p), e.shape[0] - 1, None, None, None,
+        ctypes.c_void_p(0))
 
 
 def test_static_entry_rejects_what_does_not_fit():
-    big = synth.detector_geometry(65000, 8)        # 65000 * 32 B of row tables > 2 MiB
-    with pytest.raises(dr.DrError) as ex:
-        dr.reconstruct_rows_static(big, synth.wire_path(3000), synth.bin_edges(-50, 50, 1.0),
-                                   None, None)
-    assert ex.value.status == 5 and "limit" in str(ex.value)
+    big = synth.detector_geometry(65500, 8)        # 65500 * 32 B of row tables > 2 MiB
+    assert _call_c(big, synth.wire_path(41), synth.bin_edges(-50, 50, 1.0)) == 5
+    assert "limit" in dr.lib().dr_last_error().decode()
     rot = synth.detector_geometry(8, 8, rotate_deg=10.0)
-    with pytest.raises(dr.DrError) as ex:
-        dr.reconstruct_rows_static(rot, synth.wire_path(5), synth.bin_edges(-5, 5, 1.0),
-                                   None, None)
-    assert ex.value.status == 8
+    assert _call_c(rot, synth.wire_path(5), synth.bin_edges(-5, 5, 1.0)) == 8
