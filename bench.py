@@ -45,16 +45,16 @@ PROFILE_TRAFFIC = {
     "rows": os.path.join(ROOT, "profiles", "rows_kernel_full_detector_traffic.txt"),
     "pixels": os.path.join(ROOT, "profiles", "pixels_kernel_rotated_detector_traffic.txt"),
 }
-# the rows kernel's code ends where the persistent batch kernel begins; the
-# per-pixel kernel's own section follows the batch kernel
-ROWS_KERNEL_END = "// ------------------------------------------------- persistent batch kernel ---"
-PIXELS_KERNEL_BEGIN = "// ------------------------------------------------------- pixels kernel ---"
-PIXELS_KERNEL_END = "// ------------------------------------------------ small helper kernels ---"
+# the rows kernel's code ends where the per-pixel kernel's section begins,
+# which ends where the persistent batch kernel begins
+ROWS_KERNEL_END = "// ------------------------------------------------------- pixels kernel ---"
+PIXELS_KERNEL_BEGIN = ROWS_KERNEL_END
+PIXELS_KERNEL_END = "// ------------------------------------------------- persistent batch kernel ---"
 
 
 def kernel_source_hash(kernel="rows", device_src=None, tables_src=None):
     """Hash of the code a kernel is built from: the device header up to the
-    persistent batch kernel (helpers, depth model, row tables, rows_tile,
+    per-pixel kernel's section (helpers, depth model, row tables, rows_tile,
     rows_kernel), for the per-pixel kernel also its own section, and the
     table layouts."""
     csrc = os.path.join(ROOT, "paper_2201_13309_gb300", "csrc")
@@ -432,13 +432,13 @@ def batch_waves(specs, budget_bytes):
     return waves
 
 
-def small_roi_spec(seed):
+def small_roi_spec(seed, rotate_deg=0.0):
     """A scan of the uneven-batch distribution restricted to small ROIs
     (256^2 or 512^2), where launch tails dominate a per-scan loop."""
     from tests.gen import synth
 
     for s in range(seed * 1000, seed * 1000 + 1000):
-        sp = synth.batch_scan_spec(s)
+        sp = synth.batch_scan_spec(s, rotate_deg)
         if sp.geom["rows"] <= 512:
             return sp
     raise RuntimeError("no small ROI found")
@@ -453,7 +453,7 @@ def run_batched(args, dev, specs=None):
     from tests.gen import synth
 
     if specs is None:
-        specs = [synth.batch_scan_spec(s) for s in range(args.batch_scans)]
+        specs = [synth.batch_scan_spec(s, args.rotate) for s in range(args.batch_scans)]
     waves = batch_waves(specs, args.budget_gb * 1e9)
     tot_loop = tot_batch = 0.0
     units = bytes_alg = 0.0
@@ -788,11 +788,16 @@ def main():
     if args.mode == "batched":
         if rank == 0:
             res = run_batched(args, dev)
-            small = run_batched(args, dev, [small_roi_spec(s) for s in range(args.batch_scans)])
+            small = run_batched(args, dev, [small_roi_spec(s, args.rotate)
+                                            for s in range(args.batch_scans)])
             res["small_roi_mix"] = {k: small[k] for k in ("scans", "waves", "loop", "batch",
                                                           "speedup", "bitwise_equal")}
             res["small_roi_mix"]["workload"] = ("64 scans of the same distribution restricted "
                                                 "to 256^2 and 512^2 ROIs")
+            if args.rotate:
+                rot = f"; detector rotated {args.rotate} deg (per-pixel kernel)"
+                res["workload"] += rot
+                res["small_roi_mix"]["workload"] += rot
             print(json.dumps(res), flush=True)
         return 0
     if args.mode == "served":
@@ -957,7 +962,9 @@ def main():
                        "bins": spec.B, "parallelism": f"replicas x{world}",
                        "l2": f"input ({2 * units_per_step / 1e9:.2f} GB) and output "
                              f"({4 * P * spec.B / 1e9:.1f} GB) larger than L2; no flush",
-                       "kernel": info["kernel"], "tile_cols": info["tile_cols"],
+                       "kernel": info["kernel"], "depth_series": info["depth_series"],
+                       "one_step_per_bin": info["one_step_per_bin"],
+                       "tile_cols": info["tile_cols"],
                        "pixels_per_thread": info["pixels_per_thread"],
                        "bin_groups": info["bin_groups"], "threads": info["threads"],
                        "smem_bytes": info["smem_bytes"],

@@ -125,6 +125,18 @@ typedef struct {
   size_t device_bytes;           /* device memory held by the plan */
   double bytes_per_call;         /* algorithmic HBM bytes of one
                                     dr_reconstruct: 2*P*K + out*P*B */
+  /* FP32 geometry of the rows and per-pixel kernels: the plan computes every
+   * (row or pixel, step) depth exactly as the kernels will, checks that each
+   * sequence increases by steps the fixed-point grid takes, and compares
+   * each depth with the FP64 solution of the same geometry. */
+  double max_step;               /* largest |d_{k+1} - d_k| (mm) */
+  double depth_err;              /* largest distance of a kernel depth from
+                                    the FP64 solution (mm); -1: not checked */
+  int32_t depth_series;          /* 1: the remainder's dL term by its series
+                                    (multiply-adds only), 0: exact form */
+  int32_t one_step_per_bin;      /* 1: every step at least as long as every
+                                    bin, so a bin holds at most one step */
+  int64_t checked_groups;        /* rows or pixels checked at every step */
 } dr_plan_info;
 
 /* Build a plan: validate the geometry, compute the per-pixel (or per-row,

@@ -49,7 +49,7 @@ void destroy(dr_batch_t *b) {
 
 template <class OutT>
 const void *batch_fn() {
-  return (const void *)batch_rows_kernel<OutT>;
+  return (const void *)batch_kernel<OutT>;
 }
 
 }  // namespace
@@ -83,10 +83,12 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
       set_error("dr_batch_create: job %d has no plan", i);
       return DR_ERR_INVALID_ARG;
     }
-    if (!p->parts.empty() || p->kernel != DR_KERNEL_ROWS || p->geom_prec != DR_GEOM_FP32 ||
-        p->cols % 8 != 0 || p->tune.ppt != 4) {
-      set_error("dr_batch_create: job %d: the batch runs single-run, single-edge rows-kernel "
-                "plans with FP32 geometry on widths that are multiples of 8", i);
+    const bool rows = p->kernel == DR_KERNEL_ROWS;
+    if (!p->parts.empty() || (!rows && p->kernel != DR_KERNEL_PIXELS) ||
+        p->geom_prec != DR_GEOM_FP32 || p->cols % 8 != 0 || (rows && p->tune.ppt != 4)) {
+      set_error("dr_batch_create: job %d: the batch runs single-run, single-edge plans of the "
+                "rows or per-pixel kernel with FP32 geometry on widths that are multiples of 8",
+                i);
       return DR_ERR_UNSUPPORTED;
     }
     if (out_dtype >= 0 && p->out_dtype != out_dtype) {
@@ -100,20 +102,34 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
       set_error("dr_batch_create: job %d: null or misaligned buffer", i);
       return DR_ERR_INVALID_ARG;
     }
-    // tile shape for 512-thread CTAs: the plan's width (capped by the
-    // options), narrowed until the tile fits the per-CTA budget
+    // tile shape for the batch's CTAs.  Rows tiles: the plan's width (capped
+    // by the options), narrowed until the tile fits the per-CTA budget, four
+    // pixels per thread.  Per-pixel tiles: one 32-pixel slab (8 or 16 for
+    // narrower budgets) shared by all the CTA's warps.
     Tuning t = p->tune;
-    if (opt.max_tile_cols >= 32 && t.tile_cols > opt.max_tile_cols)
-      t.tile_cols = opt.max_tile_cols / 32 * 32;
-    int smem = 0;
-    for (;;) {
-      choose_chunks(p->K, t.tile_cols, &t.kc, &t.nchunks);
-      smem = rows_smem_bytes(p->K, t.kc * t.nchunks, p->B, t.tile_cols, false);
-      if (smem <= smem_budget || t.tile_cols <= 32) break;
-      t.tile_cols /= 2;
+    int smem = 0, lanes = 0;
+    if (rows) {
+      if (opt.max_tile_cols >= 32 && t.tile_cols > opt.max_tile_cols)
+        t.tile_cols = opt.max_tile_cols / 32 * 32;
+      for (;;) {
+        choose_chunks(p->K, t.tile_cols, &t.kc, &t.nchunks);
+        smem = rows_smem_bytes(p->K, t.kc * t.nchunks, p->B, t.tile_cols, false);
+        if (smem <= smem_budget || t.tile_cols <= 32) break;
+        t.tile_cols /= 2;
+      }
+      lanes = t.tile_cols / 4;
+    } else {
+      t.tile_cols = 32;
+      for (;;) {
+        choose_chunks(p->K, t.tile_cols, &t.kc, &t.nchunks);
+        smem = pixels_smem_bytes(p->K, t.kc * t.nchunks, p->B, t.tile_cols, false);
+        if (smem <= smem_budget || t.tile_cols <= 8) break;
+        t.tile_cols /= 2;
+      }
+      lanes = t.tile_cols;
     }
-    const int lanes = t.tile_cols / 4;
-    if (smem > smem_budget || lanes > nthreads) {
+    if (smem > smem_budget || lanes > nthreads || t.kc < 1 ||
+        ((size_t)t.kc * t.tile_cols * 2) % 128 != 0) {
       set_error("dr_batch_create: job %d (%d steps) does not fit in shared memory", i, p->K);
       return DR_ERR_UNSUPPORTED;
     }
@@ -126,13 +142,15 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
     d.c = p->c;
     d.t = t;
     d.tiles_per_row = (p->cols + t.tile_cols - 1) / t.tile_cols;
+    d.kind = rows ? kBatchRows : p->one_adv ? kBatchPixelsOneAdv : kBatchPixels;
     if (P > 0) {
       dr_plan_t tmp = *p;
       tmp.tune = t;
       dr_status s = make_tensor_map(&tmp, jobs[i].d_images, &d.tmap);
       if (s != DR_OK) return s;
     }
-    cost[i] = (double)t.tile_cols * p->B;
+    // per-pixel tiles cost about twice a rows tile of the same size
+    cost[i] = (double)t.tile_cols * p->B * (rows ? 1.0 : 2.0);
   }
   // most expensive items first (the counter hands items out in order)
   std::vector<int> order(n);
@@ -210,10 +228,10 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
     if (items > 0) {
       const int ns = (int)sorted.size();
       if (out_dtype == DR_OUT_BF16)
-        batch_rows_kernel<__nv_bfloat16><<<b->grid, nthreads, smem_max, b->cap>>>(
+        batch_kernel<__nv_bfloat16><<<b->grid, nthreads, smem_max, b->cap>>>(
             b->d_scans, ns, items, b->d_counter);
       else
-        batch_rows_kernel<float><<<b->grid, nthreads, smem_max, b->cap>>>(
+        batch_kernel<float><<<b->grid, nthreads, smem_max, b->cap>>>(
             b->d_scans, ns, items, b->d_counter);
     }
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &b->graph);

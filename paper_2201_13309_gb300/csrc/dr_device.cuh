@@ -140,8 +140,39 @@ __device__ __forceinline__ uint4 zero_bits<__nv_bfloat16>(float v) {
 
 // --------------------------------------------------------- depth model ---
 
-// FP32 depth position of (group, step) in fixed point (see dr_internal.h).
-__device__ __forceinline__ int32_t depth_fx(const GroupC &g, const StepC &s, const Consts &c) {
+// float(x) for an integer 0 <= x < 2^23, exactly, on the FP32 pipe: the bit
+// pattern 0x4B000000 | x is the float 2^23 + x.
+__device__ __forceinline__ float cvt23(int32_t x) {
+  return __fsub_rn(__int_as_float(0x4B000000 | x), 8388608.0f);
+}
+
+// Round v to the nearest integer (ties to even) for |v| < 2^22: adding
+// 1.5 * 2^23 leaves the integer in the low mantissa bits.  rnd_bits returns
+// the float whose bits are 0x4B400000 + round(v) (fused with the product).
+constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23, bits 0x4B400000
+constexpr int32_t kRoundMagicBits = 0x4B400000;
+
+// FP32 depth position of (group, step) in fixed point (see dr_tables.h),
+// series form of dL (no square root or reciprocal).
+__device__ __forceinline__ int32_t depth_fx_series(const GroupC &g, const StepC &s,
+                                                   const Consts &c) {
+  const float z = s.zf;
+  const float a = __fmul_rn(c.y0, z);
+  const float tap = __fmaf_rn(a, g.invD, __fadd_rn(z, g.Q0f));
+  const float n = __fmul_rn(tap, __fsub_rn(tap, __fadd_rn(g.Z, g.Z)));
+  const float il = g.invL0;
+  const float x = __fmul_rn(n, __fmul_rn(il, il));
+  const float p = __fmaf_rn(x, __fmaf_rn(x, 0.0625f * il, -0.125f * il), 0.5f * il);
+  const float dL = __fmul_rn(n, p);
+  const float rem = __fmaf_rn(c.sR, dL, a);
+  const float r = __fmaf_rn(rem, __fmul_rn(g.invD, c.scale), kRoundMagic);
+  return (int32_t)((uint32_t)s.zfx + (uint32_t)g.Q0fx +
+                   (uint32_t)(__float_as_int(r) - kRoundMagicBits));
+}
+
+// FP32 depth position of (group, step) in fixed point, exact form of dL.
+__device__ __forceinline__ int32_t depth_fx_exact(const GroupC &g, const StepC &s,
+                                                  const Consts &c) {
   const float z = s.zf;
   float inv = g.invD;
   float a = __fmul_rn(c.y0, z);
@@ -157,6 +188,10 @@ __device__ __forceinline__ int32_t depth_fx(const GroupC &g, const StepC &s, con
   const float rem = __fmul_rn(__fmaf_rn(c.sR, dL, a), inv);
   const int32_t rfx = __float2int_rn(__fmul_rn(rem, c.scale));
   return (int32_t)((uint32_t)s.zfx + (uint32_t)g.Q0fx + (uint32_t)rfx);
+}
+
+__device__ __forceinline__ int32_t depth_fx(const GroupC &g, const StepC &s, const Consts &c) {
+  return c.depth_series ? depth_fx_series(g, s, c) : depth_fx_exact(g, s, c);
 }
 
 // Two steps of one group at once with Blackwell's packed FP32 ops (each
@@ -206,9 +241,33 @@ __device__ __forceinline__ f2 f2_sqrt(f2 x) {
 }
 __device__ __forceinline__ f2 f2_splat(float a) { return f2_pack(a, a); }
 
-// depth_fx of steps s0 and s1 of group g, step for step the same operations
-__device__ __forceinline__ void depth_fx2(const GroupC &g, const StepC &s0, const StepC &s1,
-                                          const Consts &c, int32_t &d0, int32_t &d1) {
+// depth_fx_series of steps s0 and s1 of group g, operation for operation
+__device__ __forceinline__ void depth_fx2_series(const GroupC &g, const StepC &s0,
+                                                 const StepC &s1, const Consts &c, int32_t &d0,
+                                                 int32_t &d1) {
+  const f2 z = f2_pack(s0.zf, s1.zf);
+  const f2 a = f2_mul(f2_splat(c.y0), z);
+  const f2 tap = f2_fma(a, f2_splat(g.invD), f2_add(z, f2_splat(g.Q0f)));
+  const f2 n = f2_mul(tap, f2_sub(tap, f2_splat(__fadd_rn(g.Z, g.Z))));
+  const float il = g.invL0;
+  const f2 x = f2_mul(n, f2_splat(__fmul_rn(il, il)));
+  const f2 p = f2_fma(x, f2_fma(x, f2_splat(0.0625f * il), f2_splat(-0.125f * il)),
+                      f2_splat(0.5f * il));
+  const f2 dL = f2_mul(n, p);
+  const f2 rem = f2_fma(f2_splat(c.sR), dL, a);
+  const f2 r = f2_fma(rem, f2_splat(__fmul_rn(g.invD, c.scale)), f2_splat(kRoundMagic));
+  float r0, r1;
+  f2_unpack(r, r0, r1);
+  d0 = (int32_t)((uint32_t)s0.zfx + (uint32_t)g.Q0fx +
+                 (uint32_t)(__float_as_int(r0) - kRoundMagicBits));
+  d1 = (int32_t)((uint32_t)s1.zfx + (uint32_t)g.Q0fx +
+                 (uint32_t)(__float_as_int(r1) - kRoundMagicBits));
+}
+
+// depth_fx_exact of steps s0 and s1 of group g, step for step the same operations
+__device__ __forceinline__ void depth_fx2_exact(const GroupC &g, const StepC &s0,
+                                                const StepC &s1, const Consts &c, int32_t &d0,
+                                                int32_t &d1) {
   const f2 z = f2_pack(s0.zf, s1.zf);
   f2 inv = f2_splat(g.invD);
   f2 a = f2_mul(f2_splat(c.y0), z);
@@ -228,6 +287,14 @@ __device__ __forceinline__ void depth_fx2(const GroupC &g, const StepC &s0, cons
   f2_unpack(rs, r0, r1);
   d0 = (int32_t)((uint32_t)s0.zfx + (uint32_t)g.Q0fx + (uint32_t)__float2int_rn(r0));
   d1 = (int32_t)((uint32_t)s1.zfx + (uint32_t)g.Q0fx + (uint32_t)__float2int_rn(r1));
+}
+
+__device__ __forceinline__ void depth_fx2(const GroupC &g, const StepC &s0, const StepC &s1,
+                                          const Consts &c, int32_t &d0, int32_t &d1) {
+  if (c.depth_series)
+    depth_fx2_series(g, s0, s1, c, d0, d1);
+  else
+    depth_fx2_exact(g, s0, s1, c, d0, d1);
 }
 
 // FP64 depth position of (group, step) relative to the plan origin.
@@ -264,13 +331,16 @@ struct GeoFx {
     depth_fx2(g, s0, s1, c, d0, d1);
   }
   static __device__ __forceinline__ pos_t edge(const Consts &c, int j) { return c.efx[j]; }
-  // 1 / (b - a) for a < b (approximate reciprocal; same value in both kernels)
+  // 1 / (b - a) for a < b, b - a < 2^23 (the plan checks every step):
+  // approximate reciprocal of the exactly converted length; the same value
+  // in every kernel
   static __device__ __forceinline__ float inv_len(pos_t a, pos_t b) {
-    return rcp_approx(__int2float_rn(b - a));
+    return rcp_approx(cvt23(b - a));
   }
-  static __device__ __forceinline__ float frac(pos_t e, pos_t a, float inv) {
-    float f = __fmul_rn(__int2float_rn(e - a), inv);
-    return fminf(fmaxf(f, 0.f), 1.f);
+  // Position of edge e in the interval [a, b] as a fraction: the edge is
+  // clamped to the interval first, so the difference converts exactly
+  static __device__ __forceinline__ float frac(pos_t e, pos_t a, pos_t b, float inv) {
+    return __fmul_rn(cvt23(max(min(e, b), a) - a), inv);
   }
   static __device__ __forceinline__ double to_mm(pos_t p, const Consts &c) {
     return ((double)p / (double)c.scale + c.origin) / c.nb;
@@ -298,7 +368,7 @@ struct GeoF64 {
   }
   static __device__ __forceinline__ pos_t edge(const Consts &c, int j) { return c.e64[j]; }
   static __device__ __forceinline__ double inv_len(pos_t a, pos_t b) { return 1.0 / (b - a); }
-  static __device__ __forceinline__ float frac(pos_t e, pos_t a, double inv) {
+  static __device__ __forceinline__ float frac(pos_t e, pos_t a, pos_t /*b*/, double inv) {
     double f = (e - a) * inv;
     return (float)fmin(fmax(f, 0.0), 1.0);
   }
@@ -426,7 +496,7 @@ __device__ __forceinline__ int2 build_row_table(const Consts &c, int row,
       if (spos[mid] < e) lo = mid + 1; else hi = mid;
     }
     const int k = min(max(lo - 1, 0), K - 2);
-    const float f = Geo::frac(e, spos[k], Geo::inv_len(spos[k], spos[k + 1]));
+    const float f = Geo::frac(e, spos[k], spos[k + 1], Geo::inv_len(spos[k], spos[k + 1]));
     out1[j] = make_int2(k, __float_as_int(f));
     below += !(e > tfirst);
     above += !(e < tlast);
@@ -593,58 +663,6 @@ __global__ void __launch_bounds__(512) rows_kernel(const __grid_constant__ CUten
                                   smem, 0u);
 }
 
-// ------------------------------------------------- persistent batch kernel ---
-// Many scans (each with its own plan tables, tensor map and tile shape) in
-// one launch: every CTA takes (scan, row, tile) work items from a device
-// counter until none are left.  Items are numbered scan by scan in the order
-// of the descriptor array.
-
-struct BatchScan {
-  CUtensorMap tmap;        // [K][rows][cols] images, box [kc][1][tile_cols]
-  const uint16_t *img;
-  void *out;
-  Consts c;
-  Tuning t;
-  long long item_begin;    // first work item of this scan
-  int tiles_per_row;
-  int pad;
-};
-
-template <class OutT>
-__global__ void __launch_bounds__(512, 1) batch_rows_kernel(const BatchScan *__restrict__ scans,
-                                                            int nscans, long long n_items,
-                                                            unsigned long long *counter) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  long long *slot = reinterpret_cast<long long *>(smem + 16);
-  int *sscan = reinterpret_cast<int *>(smem + 24);
-  if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
-  uint32_t parity = 0;
-  for (;;) {
-    __syncthreads();  // previous tile done with smem; barrier initialised
-    if (threadIdx.x == 0) {
-      const long long item = (long long)atomicAdd(counter, 1ull);
-      int lo = 0, hi = nscans - 1;  // last scan with item_begin <= item
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (scans[mid].item_begin <= item) lo = mid; else hi = mid - 1;
-      }
-      *slot = item;
-      *sscan = lo;
-    }
-    __syncthreads();
-    const long long item = *slot;
-    if (item >= n_items) break;
-    const BatchScan &S = scans[*sscan];
-    const long long local = item - S.item_begin;
-    const int row = (int)(local / S.tiles_per_row);
-    const int c0 = (int)(local % S.tiles_per_row) * S.t.tile_cols;
-    if (!rows_tile<GeoFx, OutT, true, 4>(&S.tmap, S.img, reinterpret_cast<OutT *>(S.out), S.c,
-                                         S.t, row, c0, smem, parity))
-      break;
-    parity ^= 1u;
-  }
-}
-
 // ------------------------------------------------------- pixels kernel ---
 // General geometry: every pixel has its own depth sequence.  A CTA owns one
 // row x tile_cols pixels x all steps; its threads are (pixel, slab, share):
@@ -661,8 +679,15 @@ __global__ void __launch_bounds__(512, 1) batch_rows_kernel(const BatchScan *__r
 //     the bins outside it, which are zero.  The bin loop is uniform over the
 //     warp, so the 32 lanes store bin j as one coalesced line.  The searches
 //     start from a linear guess and are exact (binary search as fallback).
-// A bin is zero for a pixel when e_{j+1} <= d_0 or e_j >= d_{K-1}, the same
-// rule as the rows kernel's, so both kernels give bitwise the same bins.
+// FP32 geometry (GeoFx): per bin a lane clamps the edge to its last depth,
+// advances its step at most once (more often only when the plan found a step
+// shorter than a bin), and evaluates F with integer clamps and exact 2^23-bias
+// conversions, so the bin loop keeps the conversion pipe free; F is constant
+// (and exactly zero below d_0) outside [d_0, d_{K-1}], so those bins come out
+// as exact zeros with no test.  FP64 geometry keeps the general walk with the
+// zero rule: a bin is zero for a pixel when e_{j+1} <= d_0 or e_j >= d_{K-1}.
+// Both give the rows kernel's values bitwise on row-shared geometry: (k, f)
+// come from the same device functions (GeoFx::frac / inv_len).
 // Shared-memory layout: [0, 128) mbarrier, then the image tile
 // [Kpad][tile_cols] uint16, the depth positions [K][tile_cols], the bin edges
 // [B + 1].
@@ -680,13 +705,17 @@ __device__ __forceinline__ T group_max(T v, int width) {
   return v;
 }
 
-template <class Geo, class OutT, bool kTma>
-__global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks) pixels_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                         const uint16_t *__restrict__ img,
-                                                         OutT *__restrict__ out, const Consts c,
-                                                         const Tuning t) {
+// One tile: row `row`, columns c0 .. c0 + tile_cols - 1, all steps and bins.
+// The mbarrier at smem[0] must be initialised (by thread 0 before the call,
+// or earlier with a barrier since); `parity` is its phase for this tile.
+// Returns false (for every thread) if the bounded TMA wait ran out.
+template <class Geo, class OutT, bool kTma, bool kOneAdv>
+__device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint16_t *img,
+                                            OutT *out, const Consts &c, const Tuning &t,
+                                            int row, int c0, unsigned char *smem,
+                                            uint32_t parity) {
   using pos_t = typename Geo::pos_t;
-  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr bool kFx = std::is_same<Geo, GeoFx>::value;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   uint16_t *simg = reinterpret_cast<uint16_t *>(smem + 128);
   const int TC = t.tile_cols, K = c.K, B = c.B, G = t.bin_groups;
@@ -694,7 +723,6 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks) pixels_kernel(cons
   pos_t *spos = reinterpret_cast<pos_t *>(smem + 128 + align16((size_t)Kpad * TC * 2));
   pos_t *sedge = reinterpret_cast<pos_t *>(reinterpret_cast<unsigned char *>(spos) +
                                            align16((size_t)K * TC * sizeof(pos_t)));
-  const int row = blockIdx.y, c0 = blockIdx.x * TC;
   const int tid = threadIdx.x, NT = blockDim.x;
   // slabs of SW adjacent pixels (32, or the whole tile when it is narrower);
   // thread = (pixel of its slab, slab, share)
@@ -705,19 +733,29 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks) pixels_kernel(cons
   const int ncols = min(TC, c.W - c0);
   const bool valid = lc < ncols;
 
-  if constexpr (kTma) {
-    if (tid == 0) mbar_init(bar, 1);
-  }
-  stage_tile<kTma>(&tmap, img, simg, bar, c, t, row, c0);
+  stage_tile<kTma>(tmap, img, simg, bar, c, t, row, c0);
   if (valid) {
     const auto g = Geo::group(c, row * c.W + c0 + lc);
     const auto *gsteps = Geo::steps(c);
-    for (int k = share; k < K; k += 2 * G) {  // steps k and k + G together
-      const int k2 = min(k + G, K - 1);
-      pos_t d0, d1;
-      Geo::depth2(g, gsteps[k], gsteps[k2], c, d0, d1);
-      spos[k * TC + lc] = d0;
-      if (k + G < K) spos[(k + G) * TC + lc] = d1;
+    auto fill = [&](auto depth2) {
+      for (int k = share; k < K; k += 2 * G) {  // steps k and k + G together
+        const int k2 = min(k + G, K - 1);
+        pos_t d0, d1;
+        depth2(g, gsteps[k], gsteps[k2], c, d0, d1);
+        spos[k * TC + lc] = d0;
+        if (k + G < K) spos[(k + G) * TC + lc] = d1;
+      }
+    };
+    if constexpr (kFx) {
+      if (c.depth_series)
+        fill([](const GroupC &g, const StepC &s0, const StepC &s1, const Consts &c,
+                int32_t &d0, int32_t &d1) { depth_fx2_series(g, s0, s1, c, d0, d1); });
+      else
+        fill([](const GroupC &g, const StepC &s0, const StepC &s1, const Consts &c,
+                int32_t &d0, int32_t &d1) { depth_fx2_exact(g, s0, s1, c, d0, d1); });
+    } else {
+      fill([](const auto &g, const auto &s0, const auto &s1, const Consts &c, pos_t &d0,
+              pos_t &d1) { Geo::depth2(g, s0, s1, c, d0, d1); });
     }
   }
   for (int j = tid; j <= B; j += NT) sedge[j] = Geo::edge(c, j);
@@ -744,20 +782,21 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks) pixels_kernel(cons
     return lo;
   };
   const pos_t e0 = sedge[0];
-  const float bins_per_pos = (float)B / (float)(sedge[B] - e0);
+  const float bins_per_pos = (float)B / ((float)sedge[B] - (float)e0);
   // the slab's data span [jlo, jhi): bin j can hold data for some pixel of
   // the slab only if e_{j+1} > min d_0 and e_j < max d_{K-1}; every warp
   // holds whole slabs, so each finds its own
   const pos_t lo_d = group_min(valid ? pos(0) : sedge[B], SW);
   const pos_t hi_d = group_max(valid ? pos(K - 1) : sedge[0], SW);
-  const int n_le = count_prefix((float)(lo_d - e0) * bins_per_pos + 1.f, B + 1,
+  const int n_le = count_prefix(((float)lo_d - (float)e0) * bins_per_pos + 1.f, B + 1,
                                 [&](int i) { return !(sedge[i] > lo_d); });
-  const int n_lt = count_prefix((float)(hi_d - e0) * bins_per_pos + 1.f, B + 1,
+  const int n_lt = count_prefix(((float)hi_d - (float)e0) * bins_per_pos + 1.f, B + 1,
                                 [&](int i) { return sedge[i] < hi_d; });
   const int jlo = min(max(n_le - 1, 0), B);
   const int2 sp = make_int2(jlo, max(min(n_lt, B), jlo));
   if constexpr (kTma) {
-    if (!mbar_wait_bounded(bar, 0, c.err)) return;
+    const bool late = !mbar_wait_bounded(bar, parity, c.err);
+    if (__syncthreads_or(late)) return false;
   }
   const float sign = c.out_sign, zero = __fmul_rn(sign, 0.f);
   const size_t plane = (size_t)c.H * c.W;
@@ -784,71 +823,209 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks) pixels_kernel(cons
       }
     }
   }
-  if (!valid) return;
+  if (!valid) return true;
   OutT *const o0 = out + (size_t)row * c.W + c0 + lc;
   // this share's part of the span
   const int nd = sp.y - sp.x;
   const int jb = sp.x + (int)((long long)nd * share / G);
   const int je = sp.x + (int)((long long)nd * (share + 1) / G);
-  if (jb >= je) return;
+  if (jb >= je) return true;
   const pos_t tfirst = pos(0), tlast = pos(K - 1);
   // image of step k at ip[k * istep] (steps stored in reverse for a reversed plan)
   const bool rev = c.reverse != 0;
   const uint16_t *ip = simg + (rev ? (K - 1) * TC : 0) + lc;
   const int istep = rev ? -TC : TC;
-  auto spx = [&](int k) { return biased(ip[k * istep]); };
   // k = last step below e_jb, clamped to an interval
   pos_t eb = sedge[jb];
   const int n_below = count_prefix(
-      (float)(eb - tfirst) * ((float)(K - 1) / (float)(tlast - tfirst)) + 1.f, K,
+      ((float)eb - (float)tfirst) * ((float)(K - 1) / ((float)tlast - (float)tfirst)) + 1.f, K,
       [&](int i) { return pos(i) < eb; });
   int k = min(max(n_below - 1, 0), K - 2);
-  pos_t t0 = pos(k), t1 = pos(k + 1);
-  auto inv = Geo::inv_len(t0, t1);
-  const float I0 = spx(0);
-  float Ik1 = spx(k + 1);
-  float base = __fsub_rn(I0, spx(k)), dI = __fsub_rn(spx(k), Ik1);
-  // F at edge e (k moves forward only): F = f (I_k - I_{k+1}) + (I_0 - I_k)
-  auto F_at = [&](pos_t e) {
-    while (k < K - 2 && t1 < e) {
-      ++k;
-      t0 = t1;
-      t1 = pos(k + 1);
-      inv = Geo::inv_len(t0, t1);
-      const float Ik = Ik1;
-      Ik1 = spx(k + 1);
-      base = __fsub_rn(I0, Ik);
-      dI = __fsub_rn(Ik, Ik1);
-    }
-    return __fmaf_rn(Geo::frac(e, t0, inv), dI, base);
-  };
-  float Fp = F_at(eb);
+  const float I0 = biased(ip[0]);
   OutT *o = o0 + (size_t)jb * plane;
-  if (acc) {
-    for (int j = jb; j < je; ++j, o += plane) {
-      const pos_t e1 = sedge[j + 1];
-      const float F = F_at(e1);
-      const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
-      if (e1 > tfirst && eb < tlast) st_cs(o, __fadd_rn(out_load(o), v));
-      Fp = F;
-      eb = e1;
+  if constexpr (kFx) {
+    // Walk state: t0 = t_k, t1 = t_{k+1} (pp points at t1), the image of
+    // step k + 1 (at ipn), base = I_0 - I_k, dI = I_k - I_{k+1}.  An edge
+    // is first clamped to the last depth, so the walk never passes the last
+    // interval; the clamped edge then lies in [t0, t1] (or below t0 on the
+    // first interval), and F at an edge at or above t_{K-1} is the same
+    // value for every such edge, as F below t_0 is exactly zero: the bins
+    // outside [d_0, d_{K-1}] come out as exact zeros without a test.  Each
+    // bin advances at most once when the plan found every step at least as
+    // long as every bin (kOneAdv), else as often as needed.
+    const int32_t *pp = spos + (k + 1) * TC + lc;
+    int32_t t0 = pp[-TC], t1 = *pp;
+    const uint16_t *ipn = ip + (k + 1) * istep;
+    float Ik1 = biased(*ipn);
+    const float Ik = biased(ipn[-istep]);
+    float base = __fsub_rn(I0, Ik), dI = __fsub_rn(Ik, Ik1);
+    float inv = GeoFx::inv_len(t0, t1);
+    auto advance = [&]() {
+      t0 = t1;
+      pp += TC;
+      t1 = *pp;
+      ipn += istep;
+      const float In = biased(*ipn);
+      base = __fsub_rn(I0, Ik1);
+      dI = __fsub_rn(Ik1, In);
+      Ik1 = In;
+      inv = GeoFx::inv_len(t0, t1);
+    };
+    // F at edge e: the same value as GeoFx::frac over the rows table
+    auto F_at = [&](int32_t e) {
+      const int32_t ec = min(e, tlast);
+      if (t1 < ec) advance();
+      if constexpr (!kOneAdv) {
+        while (t1 < ec) advance();
+      }
+      return __fmaf_rn(__fmul_rn(cvt23(max(ec, t0) - t0), inv), dI, base);
+    };
+    float Fp = F_at(eb);
+    if (acc) {
+      for (int j = jb; j < je; ++j, o += plane) {
+        const int32_t e1 = sedge[j + 1];
+        const float F = F_at(e1);
+        const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
+        if (e1 > tfirst && eb < tlast) st_cs(o, __fadd_rn(out_load(o), v));
+        Fp = F;
+        eb = e1;
+      }
+    } else {
+#pragma unroll 4
+      for (int j = jb; j < je; ++j, o += plane) {
+        const float F = F_at(sedge[j + 1]);
+        st_cs(o, __fmul_rn(sign, __fsub_rn(F, Fp)));
+        Fp = F;
+      }
     }
   } else {
-    // below d_0 both edges give F = 0 exactly, so only the upper test is
-    // needed for the zero rule
+    pos_t t0 = pos(k), t1 = pos(k + 1);
+    auto inv = Geo::inv_len(t0, t1);
+    float Ik1 = biased(ip[(k + 1) * istep]);
+    const float Ik = biased(ip[k * istep]);
+    float base = __fsub_rn(I0, Ik), dI = __fsub_rn(Ik, Ik1);
+    // F at edge e (k moves forward only): F = f (I_k - I_{k+1}) + (I_0 - I_k)
+    auto F_at = [&](pos_t e) {
+      while (k < K - 2 && t1 < e) {
+        ++k;
+        t0 = t1;
+        t1 = pos(k + 1);
+        inv = Geo::inv_len(t0, t1);
+        const float Ikk = Ik1;
+        Ik1 = biased(ip[(k + 1) * istep]);
+        base = __fsub_rn(I0, Ikk);
+        dI = __fsub_rn(Ikk, Ik1);
+      }
+      return __fmaf_rn(Geo::frac(e, t0, t1, inv), dI, base);
+    };
+    float Fp = F_at(eb);
+    if (acc) {
+      for (int j = jb; j < je; ++j, o += plane) {
+        const pos_t e1 = sedge[j + 1];
+        const float F = F_at(e1);
+        const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
+        if (e1 > tfirst && eb < tlast) st_cs(o, __fadd_rn(out_load(o), v));
+        Fp = F;
+        eb = e1;
+      }
+    } else {
+      // below d_0 both edges give F = 0 exactly, so only the upper test is
+      // needed for the zero rule
 #pragma unroll 2
-    for (int j = jb; j < je; ++j, o += plane) {
-      const pos_t e1 = sedge[j + 1];
-      const float F = F_at(e1);
-      const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
-      st_cs(o, eb < tlast ? v : zero);
-      Fp = F;
-      eb = e1;
+      for (int j = jb; j < je; ++j, o += plane) {
+        const pos_t e1 = sedge[j + 1];
+        const float F = F_at(e1);
+        const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
+        st_cs(o, eb < tlast ? v : zero);
+        Fp = F;
+        eb = e1;
+      }
     }
+  }
+  return true;
+}
+
+// One CTA per tile (grid: tiles along the row x rows).
+template <class Geo, class OutT, bool kTma, bool kOneAdv>
+__global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks)
+    pixels_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *__restrict__ img,
+                  OutT *__restrict__ out, const Consts c, const Tuning t) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  // thread 0 initialises the barrier and issues the copies; the others
+  // first poll it after the tile's first __syncthreads
+  if constexpr (kTma) {
+    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
+  }
+  pixels_tile<Geo, OutT, kTma, kOneAdv>(&tmap, img, out, c, t, blockIdx.y,
+                                        blockIdx.x * t.tile_cols, smem, 0u);
+}
+
+// ------------------------------------------------- persistent batch kernel ---
+// Many scans (each with its own plan tables, tensor map and tile shape) in
+// one launch: every CTA takes (scan, row, tile) work items from a device
+// counter until none are left.  Items are numbered scan by scan in the order
+// of the descriptor array.
+
+// Work-item kinds: a rows tile, or a per-pixel tile (with at most one step
+// advance per bin, or the general walk).
+enum : int { kBatchRows = 0, kBatchPixelsOneAdv = 1, kBatchPixels = 2 };
+
+struct BatchScan {
+  CUtensorMap tmap;        // [K][rows][cols] images, box [kc][1][tile_cols]
+  const uint16_t *img;
+  void *out;
+  Consts c;
+  Tuning t;
+  long long item_begin;    // first work item of this scan
+  int tiles_per_row;
+  int kind;                // kBatchRows / kBatchPixelsOneAdv / kBatchPixels
+};
+
+template <class OutT>
+__global__ void __launch_bounds__(512, 1) batch_kernel(const BatchScan *__restrict__ scans,
+                                                       int nscans, long long n_items,
+                                                       unsigned long long *counter) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  long long *slot = reinterpret_cast<long long *>(smem + 16);
+  int *sscan = reinterpret_cast<int *>(smem + 24);
+  if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
+  uint32_t parity = 0;
+  for (;;) {
+    __syncthreads();  // previous tile done with smem; barrier initialised
+    if (threadIdx.x == 0) {
+      const long long item = (long long)atomicAdd(counter, 1ull);
+      int lo = 0, hi = nscans - 1;  // last scan with item_begin <= item
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (scans[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+      }
+      *slot = item;
+      *sscan = lo;
+    }
+    __syncthreads();
+    const long long item = *slot;
+    if (item >= n_items) break;
+    const BatchScan &S = scans[*sscan];
+    const long long local = item - S.item_begin;
+    const int row = (int)(local / S.tiles_per_row);
+    const int c0 = (int)(local % S.tiles_per_row) * S.t.tile_cols;
+    OutT *const o = reinterpret_cast<OutT *>(S.out);
+    bool ok;
+    if (S.kind == kBatchRows)
+      ok = rows_tile<GeoFx, OutT, true, 4>(&S.tmap, S.img, o, S.c, S.t, row, c0, smem, parity);
+    else if (S.kind == kBatchPixelsOneAdv)
+      ok = pixels_tile<GeoFx, OutT, true, true>(&S.tmap, S.img, o, S.c, S.t, row, c0, smem,
+                                                parity);
+    else
+      ok = pixels_tile<GeoFx, OutT, true, false>(&S.tmap, S.img, o, S.c, S.t, row, c0, smem,
+                                                 parity);
+    if (!ok) break;
+    parity ^= 1u;
   }
 }
 
 // ------------------------------------------------ small helper kernels ---
+
 
 template <class Geo>
 __global__ void depths_kernel(const Consts c, int kernel, int r0, int nrows, double *out) {
@@ -949,7 +1126,7 @@ __global__ void __launch_bounds__(256) selected_kernel(const Consts c, int kerne
       Ik = Ik1;
       Ik1 = px(k + 1);
     }
-    const float f = Geo::frac(e, t0, inv);
+    const float f = Geo::frac(e, t0, t1, inv);
     const float F = __fmaf_rn(f, __fsub_rn(Ik, Ik1), __fsub_rn(I0, Ik));
     if (j > 0) {
       st_cs(o, ep < tlast ? __fmul_rn(sign, __fsub_rn(F, Fp)) : zero);

@@ -26,6 +26,12 @@ struct dr_plan {
   int threads, smem_bytes;
   size_t device_bytes;
   void *dev_block;         // single device allocation holding every table
+  // what the plan-time check of every (group, step) found (FP32 geometry of
+  // the running-sum kernels): groups checked, largest step and largest
+  // distance from FP64 in grid units (-1: not checked), and whether every
+  // step is at least as long as every bin (at most one step boundary per bin)
+  long long checked_groups = 0;
+  int max_step_units = 0, max_dev_units = -1, one_adv = 0;
   // composite plans (monotone runs of a back-and-forth scan, both wire
   // edges): the parts run in order on images + part_k0 planes, the first
   // writing the output and the others adding to it; empty for a plain plan
@@ -74,6 +80,9 @@ void choose_chunks(int K, int tile_cols, int *kc, int *nchunks);
 dr_status allow_smem(const void *fn);
 // [K][rows][cols] uint16 tensor map with a [kc][1][tile_cols] box (p->tune).
 dr_status make_tensor_map(const dr_plan_t *p, const uint16_t *img, CUtensorMap *tm);
+// Run check_kernel over the plan's ngroups groups into the device record
+// d_res and copy the result to *h_res; synchronous.
+dr_status run_plan_check(const dr_plan_t *p, int ngroups, PlanCheck *d_res, PlanCheck *h_res);
 // Build the plan's per-row (k, f) tables into tab (H rows of c.tab_stride
 // entries) on the device; synchronous.
 dr_status build_plan_tables(const dr_plan_t *p, int2 *tab);

@@ -127,9 +127,12 @@ void choose_chunks(int K, int tile_cols, int *kc, int *nchunks) {
 // One monotone plan.  side != 0 fixes the tangent side s (the wire edge
 // chosen by the whole scan's travel), for the runs of a composite plan whose
 // own travel may point the other way.
+// shift_cap bounds the fixed-point scale (a retry after the check found a
+// step too long for it); allow_series = false forces the exact form of dL.
 static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wires, int32_t K,
                           const double *edges, int32_t B, const dr_plan_options *opt_in,
-                          int side, dr_plan_t **out) {
+                          int side, dr_plan_t **out, int shift_cap = 40,
+                          bool allow_series = true) {
   if (out) *out = nullptr;
   if (!g || !wires || !edges || !out) {
     set_error("dr_plan: null argument");
@@ -276,9 +279,13 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   }
 
   // ---- FP64 depth sequences: monotonicity, range, smallest step ----
-  // Row groups: every (group, step).  Pixel groups: every pixel at the first
-  // and last step (the range) and a sub-grid of pixels at every step.
-  double tmin = 1e300, tmax = -1e300, minstep = 1e300, remmax = 0.0;
+  // Row groups: every (group, step), and a sequence that does not increase
+  // stops the plan here.  Pixel groups: every pixel at the first and last
+  // step (the range) and a sub-grid of pixels at every step, for the
+  // estimates of the range, step sizes and remainder that set the
+  // fixed-point scale; whether every pixel's sequence increases is decided
+  // by the check of every (pixel, step) on the device after the upload.
+  double tmin = 1e300, tmax = -1e300, minstep = 1e300, maxstep = 0.0, remmax = 0.0;
   auto check_group = [&](const Group64 &q, bool all_steps, int *bad_k) -> bool {
     double prev = 0;
     for (int k = 0; k < K; ++k) {
@@ -292,10 +299,16 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
         if (intervals) {  // any order: only the smallest nonzero step is kept
           if (st != 0) minstep = std::min(minstep, std::fabs(st));
         } else if (!(st > 0)) {
+          if (!rows_shared) {  // left to the device check of every pixel
+            prev = t;
+            continue;
+          }
           *bad_k = k;
           return false;
+        } else {
+          minstep = std::min(minstep, st);
+          maxstep = std::max(maxstep, st);
         }
-        else minstep = std::min(minstep, st);
       }
       prev = t;
     }
@@ -335,7 +348,14 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   for (int i = 0; i < G; ++i) mag = std::max(mag, std::fabs(grp[i].Q0));
   mag = std::max(mag, remmax * 1.5);
   int shift = (int)std::floor(std::log2((double)(1 << 29) / mag));
-  shift = std::min(shift, 40);
+  shift = std::min(shift, shift_cap);
+  // FP32 geometry of the running-sum kernels: every step must stay below
+  // 2^23 grid units (exact conversion of position differences); the check
+  // below confirms it for every (group, step) and retries with a smaller
+  // scale if a step the host did not sample is longer
+  const bool fx_walk = !intervals && opt.geom_precision == DR_GEOM_FP32;
+  if (fx_walk && maxstep > 0.0)
+    shift = std::min(shift, (int)std::floor(std::log2(0.9 * kMaxStepUnits / maxstep)));
   if (shift < 12) {
     set_error("dr_plan: depth range too large for 32-bit fixed point");
     return DR_ERR_UNSUPPORTED;
@@ -345,9 +365,32 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   // FP32 geometry positions carry a few grid units of error, so an interval
   // must span many units (zero-length intervals are exact); FP64 geometry
   // computes positions and fractions in FP64
-  if (P > 0 && opt.geom_precision == DR_GEOM_FP32 && minstep > 0.0 && minstep * scale < 64.0) {
+  if (P > 0 && opt.geom_precision == DR_GEOM_FP32 && minstep > 0.0 &&
+      minstep * scale < kMinStepUnits) {
     set_error("dr_plan: depth steps (%.3g mm) too small for the fixed-point grid", minstep);
     return DR_ERR_UNSUPPORTED;
+  }
+
+  // ---- series form of dL (dr_tables.h) ----
+  // Bound of the first dropped term, n / (2 L0) * 5/64 * x^3 / (1 - x), over
+  // the ROI (|t| <= T, |Z| <= Zmax, L0 >= Y >= Ymin), carried into the
+  // remainder (times R / D) in grid units; the remainder itself must round
+  // by the 1.5 * 2^23 construction (|rem * 2^shift| < 2^22).
+  bool series = false;
+  if (fx_walk && allow_series && !has_eta && P > 0) {
+    double Zmax = 0.0, Ymin = 1e300;
+    for (int cr = 0; cr < 4; ++cr) {
+      const double r = (cr & 1) ? H - 1 : 0, cc = (cr & 2) ? W - 1 : 0;
+      Zmax = std::max(Zmax, std::fabs(Z00 + r * Zr + cc * Zc));
+      Ymin = std::min(Ymin, Y00 + r * Yr + cc * Yc);
+    }
+    const double T = std::max(std::fabs(tmin), std::fabs(tmax)) * 1.01 + 1e-6;
+    const double n = T * (T + 2.0 * Zmax), x = n / (Ymin * Ymin);
+    if (Ymin > y0 && x < 0.5) {
+      const double drop = n / (2.0 * Ymin) * (5.0 / 64.0) * x * x * x / (1.0 - x);
+      const double units = R / (Ymin - y0) * drop * scale;
+      series = units < 0.01 && remmax * scale < (double)(1 << 21);
+    }
   }
 
   // ---- host tables ----
@@ -362,7 +405,7 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
     gc[i].D = (float)q.D;
     gc[i].Q0f = (float)q.Q0;
     gc[i].Q0fx = (int32_t)std::llround(q.Q0 * scale);
-    gc[i].pad = 0.f;
+    gc[i].invL0 = (float)(1.0 / q.L0);
     gd[i] = {q.Z, q.Y * q.Y, q.L0, q.D, q.Q0};
   }
   std::vector<StepC> sc(K);
@@ -517,6 +560,7 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   size_t o_efx = take(sizeof(int32_t) * (B + 1)), o_gd = take(sizeof(GroupD) * G);
   size_t o_sd = take(sizeof(StepD) * K), o_e64 = take(sizeof(double) * (B + 1));
   size_t o_err = take(sizeof(int32_t) * 4);
+  size_t o_chk = take(sizeof(PlanCheck));
   // per-row (k, f) tables, built once on the device below (rows kernel only;
   // above 1 GiB the tiles build their own)
   const int tab_stride = row_table_entries(B);
@@ -577,6 +621,49 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   c.out_sign = (float)((g->edge == DR_EDGE_LEADING ? 1.0 : -1.0) * (reverse ? -1.0 : 1.0));
   c.tab = nullptr;
   c.tab_stride = tab_stride;
+  c.depth_series = series ? 1 : 0;
+  p->checked_groups = 0;
+  p->max_dev_units = -1;
+  p->max_step_units = 0;
+  p->one_adv = 0;
+  if (fx_walk && P > 0) {
+    // every (group, step) as the kernels compute it, against FP64
+    PlanCheck res;
+    dr_status st = run_plan_check(p, G, reinterpret_cast<PlanCheck *>(b + o_chk), &res);
+    if (st != DR_OK) {
+      dr_plan_destroy(p);
+      return st;
+    }
+    if (res.bad != ~0ull) {
+      const long long gi = (long long)(res.bad >> 32);
+      const int k = (int)(res.bad & 0xffffffffu);
+      dr_plan_destroy(p);
+      if (res.max_step >= kMaxStepUnits && res.min_step >= kMinStepUnits && shift > 12)
+        return plan_one(intervals, g, wires, K, edges, B, opt_in, side, out, shift - 1,
+                        allow_series);
+      const long long r = rows_shared ? gi : gi / std::max(W, 1);
+      const long long cc = rows_shared ? 0 : gi % std::max(W, 1);
+      if (res.min_step <= 0) {
+        set_error("dr_plan: depth of %s (%lld,%lld) not increasing at step %d",
+                  rows_shared ? "row" : "pixel", r, cc, k);
+        return DR_ERR_NONMONOTONIC;
+      }
+      set_error("dr_plan: a depth step of %s (%lld,%lld) at step %d is outside the "
+                "fixed-point grid's range", rows_shared ? "row" : "pixel", r, cc, k);
+      return DR_ERR_UNSUPPORTED;
+    }
+    if (series && res.max_dev > 4) {  // the series is not good enough here
+      dr_plan_destroy(p);
+      return plan_one(intervals, g, wires, K, edges, B, opt_in, side, out, shift_cap, false);
+    }
+    p->checked_groups = G;
+    p->max_dev_units = res.max_dev;
+    p->max_step_units = res.max_step;
+    p->min_step = (double)res.min_step / scale / nb;
+    long long maxbin = 0;
+    for (int j = 0; j < B; ++j) maxbin = std::max(maxbin, (long long)efx[j + 1] - efx[j]);
+    p->one_adv = res.min_step >= maxbin ? 1 : 0;
+  }
   if (row_tables) {
     dr_status st = build_plan_tables(p, reinterpret_cast<int2 *>(b + o_tab));
     if (st != DR_OK) {
@@ -647,11 +734,19 @@ static dr_status plan_parts(bool intervals, const dr_geometry *g, const double *
   top->depth_min = 1e300;
   top->depth_max = -1e300;
   top->min_step = 1e300;
+  top->max_step_units = 0;
+  top->max_dev_units = -1;
+  top->one_adv = 1;
+  top->checked_groups = 0;
   for (const dr_plan_t *q : top->parts) {
     top->depth_min = std::min(top->depth_min, q->depth_min);
     top->depth_max = std::max(top->depth_max, q->depth_max);
     top->min_step = std::min(top->min_step, q->min_step);
     top->device_bytes += q->device_bytes;
+    top->max_step_units = std::max(top->max_step_units, q->max_step_units);
+    top->max_dev_units = std::max(top->max_dev_units, q->max_dev_units);
+    top->one_adv &= q->one_adv;
+    top->checked_groups = std::max(top->checked_groups, q->checked_groups);
   }
   top->c = f->c;
   top->tune = f->tune;
@@ -764,6 +859,12 @@ extern "C" dr_status dr_plan_get_info(const dr_plan_t *p, dr_plan_info *info) {
   info->depth_min = p->depth_min;
   info->depth_max = p->depth_max;
   info->min_step = p->min_step;
+  const double unit = std::ldexp(1.0, -p->shift) / (p->nb > 0 ? p->nb : 1.0);
+  info->max_step = p->max_step_units * unit;
+  info->depth_err = p->max_dev_units >= 0 ? p->max_dev_units * unit : -1.0;
+  info->depth_series = p->c.depth_series;
+  info->one_step_per_bin = p->one_adv;
+  info->checked_groups = p->checked_groups;
   info->device_bytes = p->device_bytes;
   double P = (double)p->rows * p->cols;
   info->bytes_per_call = 2.0 * P * p->K + (p->out_dtype == DR_OUT_BF16 ? 2.0 : 4.0) * P * p->B;
@@ -891,8 +992,8 @@ dr_status dr::build_rows_tables(const dr_geometry *g, const double *wires, int K
     return DR_ERR_GEOMETRY;
   }
   // per-row constants (FP64), depth range and monotonicity
-  double tmin = edges[0] * nb, tmax = edges[B] * nb, minstep = 1e300, remmax = 0.0,
-         qmax = 0.0;
+  double tmin = edges[0] * nb, tmax = edges[B] * nb, minstep = 1e300, maxstep = 0.0,
+         remmax = 0.0, qmax = 0.0;
   for (int r = 0; r < H && W > 0; ++r) {
     const double Y = Y00 + r * Yr, Z = Z00 + r * Zr, D = Y - y_first;
     const double L0 = std::sqrt(Y * Y + Z * Z), Q0 = (-y_first * Z + sR * L0) / D;
@@ -909,6 +1010,7 @@ dr_status dr::build_rows_tables(const dr_geometry *g, const double *wires, int K
           return DR_ERR_NONMONOTONIC;
         }
         minstep = std::min(minstep, t - prev);
+        maxstep = std::max(maxstep, t - prev);
       }
       prev = t;
     }
@@ -917,12 +1019,15 @@ dr_status dr::build_rows_tables(const dr_geometry *g, const double *wires, int K
   double mag = std::max(0.5 * (tmax - tmin) * 1.001 + 1e-9, std::max(qmax, remmax * 1.5));
   for (int k = 0; k < K; ++k) mag = std::max(mag, std::fabs(zp[k] - origin));
   int shift = std::min((int)std::floor(std::log2((double)(1 << 29) / mag)), 40);
+  // every step below 2^23 grid units (exact conversion of position differences)
+  if (maxstep > 0.0)
+    shift = std::min(shift, (int)std::floor(std::log2(0.9 * kMaxStepUnits / maxstep)));
   if (shift < 12) {
     set_error("depth range too large for 32-bit fixed point");
     return DR_ERR_UNSUPPORTED;
   }
   const double scale = std::ldexp(1.0, shift);
-  if (H > 0 && W > 0 && minstep * scale < 64.0) {
+  if (H > 0 && W > 0 && minstep * scale < kMinStepUnits) {
     set_error("depth steps too small for the fixed-point grid");
     return DR_ERR_UNSUPPORTED;
   }
@@ -962,6 +1067,7 @@ dr_status dr::build_rows_tables(const dr_geometry *g, const double *wires, int K
     gc[r].D = (float)D;
     gc[r].Q0f = (float)Q0;
     gc[r].Q0fx = (int32_t)std::llround(Q0 * scale);
+    gc[r].invL0 = (float)(1.0 / L0);
   }
   StepC *sc = reinterpret_cast<StepC *>(stage + o_stp);
   for (int k = 0; k < K; ++k) {

@@ -12,7 +12,8 @@
 //  pixels_kernel  every pixel has its own depth sequence: the tile's depth
 //                 positions go to shared memory once, then the warps split
 //                 the bins evenly and each lane walks its pixel's steps and
-//                 bins together (merge-walk).
+//                 bins together (merge-walk), one step advance per bin when
+//                 the plan found every step at least as long as every bin.
 //  intervals_kernel  depths in any order (dr_intervals.cuh): every interval
 //                 is added by itself into shared-memory accumulators.
 //
@@ -36,6 +37,52 @@
 #include "dr_intervals.cuh"
 
 namespace dr {
+
+// Plan-time check of every (group, step) of an FP32-geometry plan: one
+// thread per group computes the K depth positions exactly as the kernels do
+// and the FP64 solution of the same geometry, and records (PlanCheck) the
+// first group whose positions are not strictly increasing with steps in
+// [kMinStepUnits, kMaxStepUnits), the smallest and largest step, and the
+// largest distance from the FP64 solution, in grid units.  res must hold
+// bad = ~0, min_step = INT32_MAX, max_step = max_dev = 0 before the launch.
+__global__ void __launch_bounds__(256) check_kernel(const Consts c, int ngroups,
+                                                   PlanCheck *res) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int32_t lmin = 0x7fffffff, lmax = 0, ldev = 0;
+  unsigned long long bad = ~0ull;
+  if (i < ngroups) {
+    const GroupC g = c.grp[i];
+    const GroupD gd = c.grp64[i];
+    const double scale = (double)c.scale;
+    long long prev = 0;
+    for (int k = 0; k < c.K; ++k) {
+      const int32_t t = depth_fx(g, c.stp[k], c);
+      const double ref = rint(depth_f64(gd, c.stp64[k], c) * scale);
+      ldev = max(ldev, (int32_t)fmin(fabs((double)t - ref), 2.0e9));
+      if (k > 0) {
+        const long long st = (long long)t - prev;
+        lmin = (int32_t)min((long long)lmin, max(st, -2000000000ll));
+        lmax = (int32_t)max((long long)lmax, min(st, 2000000000ll));
+        if ((st < kMinStepUnits || st >= kMaxStepUnits) && bad == ~0ull)
+          bad = ((unsigned long long)i << 32) | (unsigned)k;
+      }
+      prev = t;
+    }
+  }
+  for (int m = 16; m > 0; m >>= 1) {
+    lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, m));
+    lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, m));
+    ldev = max(ldev, __shfl_xor_sync(0xffffffffu, ldev, m));
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, bad, m);
+    bad = o < bad ? o : bad;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&res->min_step, lmin);
+    atomicMax(&res->max_step, lmax);
+    atomicMax(&res->max_dev, ldev);
+    if (bad != ~0ull) atomicMin(&res->bad, bad);
+  }
+}
 
 // Exact differences I_k - I_{k+1} as the kernels form them (int32 out).
 __global__ void differences_kernel(const uint16_t *__restrict__ img, long long n_out,
@@ -98,7 +145,12 @@ dr_status launch_rows(const dr_plan_t *p, const CUtensorMap &tm, const uint16_t 
 template <class Geo, class OutT, bool kTma>
 dr_status launch_pixels(const dr_plan_t *p, const CUtensorMap &tm, const uint16_t *img,
                         void *out, cudaStream_t st) {
-  auto fn = pixels_kernel<Geo, OutT, kTma>;
+  // FP32 geometry: the walk takes at most one step per bin when the plan's
+  // check found every step at least as long as every bin
+  auto fn = pixels_kernel<Geo, OutT, kTma, false>;
+  if constexpr (std::is_same<Geo, GeoFx>::value) {
+    if (p->one_adv) fn = pixels_kernel<Geo, OutT, kTma, true>;
+  }
   dr_status s = allow_smem((const void *)fn);
   if (s != DR_OK) return s;
   dim3 grid((p->cols + p->tune.tile_cols - 1) / p->tune.tile_cols, p->rows);
@@ -137,6 +189,27 @@ dr_status dispatch_out(const dr_plan_t *p, bool tma, const CUtensorMap &tm, cons
 
 }  // namespace
 
+dr_status run_plan_check(const dr_plan_t *p, int ngroups, PlanCheck *d_res, PlanCheck *h_res) {
+  PlanCheck init;
+  std::memset(&init, 0, sizeof(init));
+  init.bad = ~0ull;
+  init.min_step = 0x7fffffff;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail("plan check: stream", e);
+  e = cudaMemcpyAsync(d_res, &init, sizeof(init), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && ngroups > 0) {
+    check_kernel<<<(ngroups + 255) / 256, 256, 0, st>>>(p->c, ngroups, d_res);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_res, d_res, sizeof(*h_res), cudaMemcpyDeviceToHost, st);
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail("plan check", e);
+  return DR_OK;
+}
+
 dr_status build_plan_tables(const dr_plan_t *p, int2 *tab) {
   const bool f64 = p->geom_prec == DR_GEOM_FP64;
   const size_t smem = 16 + (size_t)p->K * (f64 ? 8 : 4);
@@ -168,10 +241,15 @@ dr_status preload_kernels() {
       (const void *)rows_kernel<GeoFx, __nv_bfloat16, false, 4>,
       (const void *)rows_kernel<GeoFx, __nv_bfloat16, true, 1>,
       (const void *)rows_kernel<GeoFx, __nv_bfloat16, false, 1>,
-      (const void *)pixels_kernel<GeoFx, float, true>,
-      (const void *)pixels_kernel<GeoFx, float, false>,
-      (const void *)pixels_kernel<GeoFx, __nv_bfloat16, true>,
-      (const void *)pixels_kernel<GeoFx, __nv_bfloat16, false>,
+      (const void *)pixels_kernel<GeoFx, float, true, true>,
+      (const void *)pixels_kernel<GeoFx, float, false, true>,
+      (const void *)pixels_kernel<GeoFx, __nv_bfloat16, true, true>,
+      (const void *)pixels_kernel<GeoFx, __nv_bfloat16, false, true>,
+      (const void *)pixels_kernel<GeoFx, float, true, false>,
+      (const void *)pixels_kernel<GeoFx, float, false, false>,
+      (const void *)pixels_kernel<GeoFx, __nv_bfloat16, true, false>,
+      (const void *)pixels_kernel<GeoFx, __nv_bfloat16, false, false>,
+      (const void *)check_kernel,
       (const void *)intervals_kernel<GeoFx, float, true>,
       (const void *)intervals_kernel<GeoFx, float, false>,
       (const void *)intervals_kernel<GeoFx, __nv_bfloat16, true>,

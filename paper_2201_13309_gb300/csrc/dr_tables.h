@@ -23,6 +23,14 @@
 // 2^-shift mm of projected depth relative to a plan origin, so differences of
 // positions are exact.  dL enters scaled by R / D ~ 5e-5, so evaluating it
 // at the estimate without the dL term leaves an error ~1e-10 mm.
+//
+// dL itself has two forms.  The exact one takes a square root and a
+// reciprocal: dL = t (t - 2Z) / (L(t) + L0).  With n = t (t - 2Z) =
+// L(t)^2 - L0^2 and x = n / L0^2 it is also L0 (sqrt(1 + x) - 1) =
+// n / (2 L0) (1 - x/4 + x^2/8 - 5x^3/64 + ...); the series form keeps three
+// terms (only multiply-adds).  A plan uses the series where the first dropped
+// term stays far below one grid unit, and its check compares every depth the
+// kernels compute with the FP64 solution.
 #pragma once
 
 #include <cstddef>
@@ -36,7 +44,7 @@ struct GroupC {
   float Z, Y2, L0, invD;   // FP32 copies of FP64 values
   float D, Q0f;
   int32_t Q0fx;            // round(Q0 * 2^shift)
-  float pad;
+  float invL0;             // 1 / L0 (series form of dL)
 };
 static_assert(sizeof(GroupC) == 32, "GroupC layout");
 
@@ -80,7 +88,27 @@ struct Consts {
   // 1: add this plan's bins to the output instead of writing them (the later
   // parts of a composite plan: monotone runs, both wire edges)
   int accumulate;
+  // 1: FP32 geometry evaluates dL by its series (see above), 0: exact form
+  int depth_series;
 };
+
+// What the plan-time check of every (group, step) found (device, written by
+// check_kernel): the first group whose FP32 depth positions are not strictly
+// increasing with steps in [kMinStepUnits, kMaxStepUnits), the smallest and
+// largest step, and the largest distance of an FP32 position from the FP64
+// solution, all in grid units.
+struct PlanCheck {
+  unsigned long long bad;  // (group << 32) | step of the first failure; ~0 if none
+  int32_t min_step, max_step;
+  int32_t max_dev;         // max |t_fp32 - round(t_fp64 * 2^shift)|
+  int32_t pad;
+};
+// Steps of FP32 positions must span at least this many grid units (a few
+// units of FP32 error then move a negligible part of an interval's
+// difference across a bin edge) and fewer than 2^23 (so that a position
+// difference converts to float exactly by the 2^23-bias construction).
+constexpr int32_t kMinStepUnits = 64;
+constexpr int32_t kMaxStepUnits = 1 << 23;
 
 // Entries of one row table: a header, B + 1 edges, rounded up to an even
 // count so that a row is a multiple of 16 bytes (bulk-copy granule).

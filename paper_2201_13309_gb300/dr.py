@@ -63,7 +63,9 @@ class PlanInfo(ctypes.Structure):
         "geom_precision", "edge", "reversed", "fixed_shift", "row_tables", "parts")] + [
         ("depth_min", ctypes.c_double), ("depth_max", ctypes.c_double),
         ("min_step", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-        ("bytes_per_call", ctypes.c_double)]
+        ("bytes_per_call", ctypes.c_double), ("max_step", ctypes.c_double),
+        ("depth_err", ctypes.c_double), ("depth_series", ctypes.c_int32),
+        ("one_step_per_bin", ctypes.c_int32), ("checked_groups", ctypes.c_int64)]
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_}

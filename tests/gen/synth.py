@@ -324,9 +324,11 @@ ROI_CHOICES = ((256, 256), (512, 512), (1024, 1024), (2048, 1024), (2048, 2048))
 BIN_WIDTHS_UM = (0.5, 1.0, 2.0)
 
 
-def batch_scan_spec(seed):
+def batch_scan_spec(seed, rotate_deg=0.0):
     """One scan of the uneven batch: ROI, step count and bin width drawn from
-    the seeded distribution; scatterer count 200 * area / 2048^2 (min 5)."""
+    the seeded distribution; scatterer count 200 * area / 2048^2 (min 5).
+    rotate_deg turns the detector in its plane (every pixel then has its own
+    depth sequence)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     rows, cols = ROI_CHOICES[int(rng.integers(0, len(ROI_CHOICES)))]
     K = int(rng.integers(51, 802))
@@ -334,7 +336,7 @@ def batch_scan_spec(seed):
     r0 = int(rng.integers(0, FULL_DET - rows + 1))
     c0 = int(rng.integers(0, FULL_DET - cols + 1))
     n_scat = max(5, int(round(200 * rows * cols / FULL_DET ** 2)))
-    geom = detector_geometry(rows, cols, (r0, c0), FULL_DET, FULL_DET)
+    geom = detector_geometry(rows, cols, (r0, c0), FULL_DET, FULL_DET, rotate_deg=rotate_deg)
     wires = wire_path(K)
     scat = spot_scatterers(rng, n_scat, rows, cols)
     return Scan(geom, wires, bin_edges(-400.0, 400.0, width), None, scat,

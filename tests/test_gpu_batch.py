@@ -127,13 +127,53 @@ def test_batch_replay_with_new_images():
     assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
 
 
+def _rotated_scans():
+    """Scans on a rotated (and tilted) detector: every pixel has its own
+    depth sequence, so their plans take the per-pixel kernel; one with bins
+    wider than its steps (more than one step per bin)."""
+    a = synth.spot_scan(41, 12, 96, 45, 8, -60.0, 60.0, 1.0, rotate_deg=10.0,
+                        depth_range=(-0.03, 0.03))
+    b = synth.spot_scan(42, 6, 200, 33, 6, -50.0, 60.0, 2.0, rotate_deg=-7.0, tilt_deg=4.0,
+                        depth_range=(-0.03, 0.03))
+    c = synth.spot_scan(43, 9, 64, 61, 6, -60.0, 80.0, 0.5, rotate_deg=3.0,
+                        depth_range=(-0.03, 0.03))
+    return [(a, "leading"), (b, "leading"), (c, "trailing")]
+
+
+@pytest.mark.parametrize("per_sm,nt", [(1, 512), (2, 512), (1, 256)])
+def test_batch_of_rows_and_per_pixel_plans(per_sm, nt):
+    """Rows and per-pixel tiles in one persistent launch: every scan bitwise
+    as its own launch, and each per-pixel scan against the FP64 oracle."""
+    jobs, refs, keep = [], [], []
+    for sc, edge in _scans()[:2] + _rotated_scans():
+        plan = dr.Plan(sc.geom, sc.wires, sc.edges, edge=edge)
+        img = _dev(sc.images)
+        refs.append(plan.reconstruct(img))
+        jobs.append((plan, img, torch.full_like(refs[-1], float("nan"))))
+        keep.append((sc, edge, plan.info()))
+    kinds = [k[2]["kernel"] for k in keep]
+    assert kinds == ["rows", "rows", "pixels", "pixels", "pixels"]
+    assert [k[2]["one_step_per_bin"] for k in keep[2:]] == [1, 0, 1]
+    batch = dr.Batch(jobs, ctas_per_sm=per_sm, threads=nt)
+    batch.launch()
+    torch.cuda.synchronize()
+    batch.check_device()
+    for (_, _, out), ref in zip(jobs, refs):
+        assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
+    for (sc, edge, _), (_, _, out) in zip(keep[2:], jobs[2:]):
+        want = O.reconstruct(sc.geom, sc.wires, sc.images, sc.edges, edge)
+        s = np.abs(np.diff(sc.images.astype(np.int64), axis=0)).sum(0)[None]
+        assert np.all(np.abs(out.cpu().numpy().astype(np.float64) - want) <= 1e-4 * s)
+
+
 def test_batch_rejects_unsupported_jobs():
     sc = synth.tiny_scan(35, rows=4, cols=64, K=9)
-    pix = dr.Plan(sc.geom, sc.wires, sc.edges, force_pixels=True)
-    img = _dev(sc.images)
-    with pytest.raises(dr.DrError) as ex:
-        dr.Batch([(pix, img, pix.empty_output())])
-    assert ex.value.status == 8
+    for kw in ({"force_intervals": True}, {"geom_precision": "fp64", "force_pixels": True}):
+        pix = dr.Plan(sc.geom, sc.wires, sc.edges, **kw)
+        img = _dev(sc.images)
+        with pytest.raises(dr.DrError) as ex:
+            dr.Batch([(pix, img, pix.empty_output())])
+        assert ex.value.status == 8
     odd = synth.tiny_scan(36, rows=4, cols=12, K=9)
     p2 = dr.Plan(odd.geom, odd.wires, odd.edges)
     with pytest.raises(dr.DrError):
