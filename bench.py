@@ -537,7 +537,14 @@ def run_served(args, dev):
     """Poisson arrival streams of scans from the uneven-batch distribution into
     the server (admission against an HBM budget, pinned uploads overlapped on
     slot streams, results left on the device until the client releases them);
-    plus a saturation run against a serial upload-then-reconstruct loop."""
+    plus a saturation run against a serial plan-upload-reconstruct loop.
+
+    Every request is a scan of its own (batch_scan_spec of a seed of its own:
+    its ROI origin and size, step count and bin width), so every request
+    builds its plan.  Its images are the first K planes of one pinned
+    forward-model scan per ROI size with the largest step count of the
+    distribution (1000 distinct multi-GB scans do not fit in host memory;
+    the kernels' time does not depend on the counts)."""
     import threading as th
 
     import torch
@@ -545,41 +552,44 @@ def run_served(args, dev):
     from paper_2201_13309_gb300 import dr
     from tests.gen import synth
 
-    pool, up_gbs = [], []
     placement = near_gpu(dev)
-    for s in range(args.pool):
-        sp = synth.batch_scan_spec(s)
-        img = synth.device_spot_images(sp.geom, sp.wires, sp.scat, seed=2000 + s,
-                                       background=20.0, device=dev)
+    kmax = 801
+    buffers, up_gbs = {}, {}
+    for i, (rows, cols) in enumerate(synth.ROI_CHOICES):
+        rng = np.random.Generator(np.random.PCG64(3000 + i))
+        geom = synth.detector_geometry(rows, cols, (0, 0), synth.FULL_DET, synth.FULL_DET)
+        wires = synth.wire_path(kmax)
+        scat = synth.spot_scatterers(rng, max(5, int(round(200 * rows * cols / 2048 ** 2))),
+                                     rows, cols)
+        img = synth.device_spot_images(geom, wires, scat, seed=2000 + i, background=20.0,
+                                       device=dev)
         with placement:
             h = torch.empty(img.shape, dtype=torch.int16, pin_memory=True)
             h.copy_(img)
-        # one timed upload of this pinned buffer (placement check)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         img.copy_(h, non_blocking=True)
         torch.cuda.synchronize()
-        up_gbs.append(h.numel() * 2 / (time.perf_counter() - t0) / 1e9)
-        pool.append((sp, h))
+        up_gbs[f"{rows}x{cols}"] = h.numel() * 2 / (time.perf_counter() - t0) / 1e9
+        buffers[(rows, cols)] = h
         del img
     torch.cuda.empty_cache()
+
+    def images_of(sp):
+        return buffers[(sp.geom["rows"], sp.geom["cols"])][:sp.K]
+
     budget = int(args.budget_gb * 1e9)
     results = []
     rates = [float(r) for r in args.rates.split(",") if r]
     srv = dr.Server(budget, slots=args.slots)
-    cold = []
-    for sp, h in pool:  # first request of each geometry: builds its plan
-        rid = srv.submit(sp.geom, sp.wires, sp.edges, h)
-        srv.wait(rid)
-        _, t = srv.fetch(rid)
-        cold.append((t["done"] - t["submitted"]) * 1e3)
-        srv.release(rid)
-    for rate in rates:
+    for ri, rate in enumerate(rates):
+        specs = [synth.batch_scan_spec(100000 * (ri + 1) + i) for i in range(args.served_scans)]
         rng = np.random.Generator(np.random.PCG64(1000 + int(rate)))
         gaps = rng.exponential(1.0 / rate, args.served_scans)
         ids, lat, parts = [], [], []
         lock = th.Lock()
         have = th.Semaphore(0)
+        built0 = srv.stats()["plans_built"]
 
         def consumer():
             for i in range(args.served_scans):
@@ -589,7 +599,8 @@ def run_served(args, dev):
                 srv.wait(rid)
                 _, t = srv.fetch(rid)
                 lat.append(t["done"] - t["submitted"])
-                parts.append((i % len(pool), t["admitted"] - t["submitted"],
+                sp = specs[i]
+                parts.append((sp.P * sp.K * 2, t["admitted"] - t["submitted"],
                               t["planned"] - t["admitted"], t["uploaded"] - t["planned"],
                               t["done"] - t["uploaded"]))
                 srv.release(rid)
@@ -603,8 +614,8 @@ def run_served(args, dev):
             d = nxt - time.perf_counter()
             if d > 0:
                 time.sleep(d)
-            sp, h = pool[i % len(pool)]
-            rid = srv.submit(sp.geom, sp.wires, sp.edges, h)
+            sp = specs[i]
+            rid = srv.submit(sp.geom, sp.wires, sp.edges, images_of(sp))
             with lock:
                 ids.append(rid)
             have.release()
@@ -612,73 +623,70 @@ def run_served(args, dev):
         wall = time.perf_counter() - t0
         lat_ms = np.array(lat) * 1e3
         pa = np.array([p[1:] for p in parts]) * 1e3
-        per_scan = {}
-        for (idx, q, pl, u, k), l in zip(parts, lat_ms):
-            per_scan.setdefault(idx, []).append(l)
+        in_gb = np.array([p[0] for p in parts]) / 1e9
+        big = in_gb >= np.percentile(in_gb, 90)
+        names = ("queue", "plan", "upload", "kernel")
         results.append({"offered_scans_per_s": rate, "scans": args.served_scans,
                         "achieved_scans_per_s": args.served_scans / wall,
+                        "plans_built": srv.stats()["plans_built"] - built0,
                         "p50_ms": float(np.percentile(lat_ms, 50)),
                         "p99_ms": float(np.percentile(lat_ms, 99)),
                         "mean_ms": float(lat_ms.mean()), "max_ms": float(lat_ms.max()),
-                        "phase_p50_ms": {n: float(np.percentile(pa[:, c], 50)) for c, n in
-                                         enumerate(("queue", "plan", "upload", "kernel"))},
-                        "phase_p99_ms": {n: float(np.percentile(pa[:, c], 99)) for c, n in
-                                         enumerate(("queue", "plan", "upload", "kernel"))},
-                        "per_pool_scan_median_ms": {
-                            f"{pool[i][0].geom['rows']}x{pool[i][0].geom['cols']}"
-                            f"_K{pool[i][0].K}_B{pool[i][0].B}": float(np.median(v))
-                            for i, v in sorted(per_scan.items())}})
+                        "phase_p50_ms": {n: float(np.percentile(pa[:, c], 50))
+                                         for c, n in enumerate(names)},
+                        "phase_p99_ms": {n: float(np.percentile(pa[:, c], 99))
+                                         for c, n in enumerate(names)},
+                        "largest_tenth_inputs": {
+                            "input_GB_min": float(in_gb[big].min()),
+                            "p50_ms": float(np.percentile(lat_ms[big], 50)),
+                            "upload_p50_ms": float(np.percentile(pa[big, 2], 50)),
+                            "upload_GBps_p50": float(np.percentile(
+                                in_gb[big] / np.maximum(pa[big, 2] * 1e-3, 1e-9), 50))}})
         print(json.dumps({"served_rate": results[-1]}), file=sys.stderr, flush=True)
     st = srv.stats()
     srv.close()
-    # saturation: everything submitted at once, against the serial loop
+    # saturation: everything submitted at once, against the serial loop over
+    # the same scans (plan, upload, reconstruct, one after the other)
     n_sat = args.saturation_scans
+    sat_specs = [synth.batch_scan_spec(900000 + i) for i in range(n_sat)]
     srv = dr.Server(budget, slots=args.slots)
-    for sp, h in pool:  # warm this server's plan cache
-        rid = srv.submit(sp.geom, sp.wires, sp.edges, h)
-        srv.wait(rid)
-        srv.release(rid)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ids = [srv.submit(pool[i % len(pool)][0].geom, pool[i % len(pool)][0].wires,
-                      pool[i % len(pool)][0].edges, pool[i % len(pool)][1]) for i in range(n_sat)]
+    ids = [srv.submit(sp.geom, sp.wires, sp.edges, images_of(sp)) for sp in sat_specs]
     for rid in ids:
         srv.wait(rid)
         srv.release(rid)
     t_srv = time.perf_counter() - t0
     srv.close()
-    plans = [dr.Plan(sp.geom, sp.wires, sp.edges) for sp, _ in pool]
-    d_img = torch.empty(max(h.numel() for _, h in pool), dtype=torch.int16, device=dev)
-    d_out = torch.empty(max(sp.P * sp.B for sp, _ in pool), dtype=torch.float32, device=dev)
+    d_img = torch.empty(max(h.numel() for h in buffers.values()), dtype=torch.int16, device=dev)
+    d_out = torch.empty(max(sp.P * sp.B for sp in sat_specs), dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i in range(n_sat):
-        sp, h = pool[i % len(pool)]
-        p = plans[i % len(pool)]
+    for sp in sat_specs:
+        h = images_of(sp)
+        p = dr.Plan(sp.geom, sp.wires, sp.edges)
         di = d_img[:h.numel()].view(h.shape)
         do = d_out[:sp.P * sp.B].view(sp.B, sp.geom["rows"], sp.geom["cols"])
         with torch.cuda.stream(stream):
             di.copy_(h, non_blocking=True)
             p.reconstruct(di, do, stream=stream)
         stream.synchronize()
+        p.close()
     t_loop = time.perf_counter() - t0
-    mean_in = float(np.mean([h.numel() * 2 for _, h in pool])) / 1e9
+    mean_in = float(np.mean([sp.P * sp.K * 2 for sp in sat_specs])) / 1e9
     return {"mode": "served", "metric": "scans/s and p50/p99 latency (arrival -> result on device)",
-            "budget_GB": args.budget_gb, "slots": args.slots, "pool_scans": len(pool),
-            "pinned_upload_GBps": {"min": float(min(up_gbs)), "median": float(np.median(up_gbs)),
-                                   "max": float(max(up_gbs))},
-            "alloc_cpus": placement.cpus,
+            "budget_GB": args.budget_gb, "slots": args.slots,
+            "pinned_upload_GBps": up_gbs, "alloc_cpus": placement.cpus,
             "mean_input_GB": mean_in, "rates": results,
-            "plan_cache": {"plans_built": st["plans_built"], "failed": st["failed"],
-                           "cold_first_request_ms": {"p50": float(np.percentile(cold, 50)),
-                                                     "max": float(np.max(cold))}},
+            "plan_cache": {"plans_built": st["plans_built"], "failed": st["failed"]},
             "saturation": {"scans": n_sat, "server_scans_per_s": n_sat / t_srv,
                            "serial_loop_scans_per_s": n_sat / t_loop,
                            "speedup": t_loop / t_srv},
-            "workload": ("requests cycle over a pool of distinct scans from the uneven-batch "
-                         "distribution (ROI 256^2..2048^2, 51-801 steps, 0.5/1/2 um bins over "
-                         "+-400 um) held in pinned host memory")}
+            "workload": ("every request a scan of its own from the uneven-batch distribution "
+                         "(ROI 256^2..2048^2 at its own origin, 51-801 steps, 0.5/1/2 um bins "
+                         "over +-400 um), so every request builds its plan; images are the "
+                         "first K planes of one pinned forward-model scan per ROI size")}
 
 
 def run_pixels(args, spec, images, dev):
@@ -741,7 +749,6 @@ def main():
     ap.add_argument("--rates", default="5,20,50")
     ap.add_argument("--served-scans", type=int, default=1000)
     ap.add_argument("--saturation-scans", type=int, default=96)
-    ap.add_argument("--pool", type=int, default=16)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--batch-scans", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
@@ -829,6 +836,12 @@ def main():
 
     out = torch.empty((spec.B, spec.geom["rows"], spec.geom["cols"]), dtype=torch.float32,
                       device=dev)
+    # plan-build time of this workload (host sample, device constants and the
+    # check of every (group, step)), outside the timed region
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter()
+    dr.Plan(spec.geom, spec.wires, spec.edges, force_intervals=args.intervals).close()
+    plan_ms = (time.perf_counter() - t_plan) * 1e3
     if args.intervals:
         plan = dr.Plan(spec.geom, spec.wires, spec.edges, force_intervals=True)
         tuned = None
@@ -884,7 +897,11 @@ def main():
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": peak_kind,
                 "kernel": {"rows": "rows_kernel<GeoFx,float,tma,4>",
-                           "pixels": "pixels_kernel<GeoFx,float,tma>",
+                           "pixels": ("pixels_poly_kernel<float,tma,"
+                                      f"one_step={info['one_step_per_bin']}>"
+                                      if info["depth_form"] == 2 else
+                                      f"pixels_kernel<GeoFx,float,tma,"
+                                      f"one_step={info['one_step_per_bin']}>"),
                            "intervals": "intervals_kernel<GeoFx,float,tma>"}[info["kernel"]],
                 "algorithmic_bytes_per_launch": alg_bytes}
 
@@ -962,7 +979,8 @@ def main():
                        "bins": spec.B, "parallelism": f"replicas x{world}",
                        "l2": f"input ({2 * units_per_step / 1e9:.2f} GB) and output "
                              f"({4 * P * spec.B / 1e9:.1f} GB) larger than L2; no flush",
-                       "kernel": info["kernel"], "depth_series": info["depth_series"],
+                       "kernel": info["kernel"], "depth_form": info["depth_form"],
+                       "plan_ms": round(plan_ms, 1),
                        "one_step_per_bin": info["one_step_per_bin"],
                        "tile_cols": info["tile_cols"],
                        "pixels_per_thread": info["pixels_per_thread"],

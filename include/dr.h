@@ -98,7 +98,11 @@ typedef struct {
                                pixels of a row share their depths */
   int32_t force_intervals;  /* 1: use the interval kernel (depths in any
                                order) even when every sequence is monotone */
-  int32_t reserved[2];
+  int32_t depth_form;       /* FP32 geometry: 0 = the plan's choice; else the
+                               cheapest form the plan may use for the depth
+                               remainder, plus one: 1 exact, 2 up to the
+                               series of dL, 3 up to the per-pixel cubic */
+  int32_t reserved;
 } dr_plan_options;
 
 typedef struct dr_plan dr_plan_t;
@@ -132,8 +136,10 @@ typedef struct {
   double max_step;               /* largest |d_{k+1} - d_k| (mm) */
   double depth_err;              /* largest distance of a kernel depth from
                                     the FP64 solution (mm); -1: not checked */
-  int32_t depth_series;          /* 1: the remainder's dL term by its series
-                                    (multiply-adds only), 0: exact form */
+  int32_t depth_form;            /* form of the FP32 remainder: 0 exact (a
+                                    square root and a reciprocal), 1 series
+                                    of dL, 2 per-pixel cubic in the wire
+                                    position (multiply-adds only) */
   int32_t one_step_per_bin;      /* 1: every step at least as long as every
                                     bin, so a bin holds at most one step */
   int64_t checked_groups;        /* rows or pixels checked at every step */

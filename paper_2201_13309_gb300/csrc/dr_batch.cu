@@ -120,9 +120,11 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
       lanes = t.tile_cols / 4;
     } else {
       t.tile_cols = 32;
+      const bool poly = p->c.depth_mode == kDepthPoly;
       for (;;) {
         choose_chunks(p->K, t.tile_cols, &t.kc, &t.nchunks);
-        smem = pixels_smem_bytes(p->K, t.kc * t.nchunks, p->B, t.tile_cols, false);
+        smem = poly ? pixels_poly_smem_bytes(p->K, t.kc * t.nchunks, p->B, t.tile_cols)
+                    : pixels_smem_bytes(p->K, t.kc * t.nchunks, p->B, t.tile_cols, false);
         if (smem <= smem_budget || t.tile_cols <= 8) break;
         t.tile_cols /= 2;
       }
@@ -142,7 +144,12 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
     d.c = p->c;
     d.t = t;
     d.tiles_per_row = (p->cols + t.tile_cols - 1) / t.tile_cols;
-    d.kind = rows ? kBatchRows : p->one_adv ? kBatchPixelsOneAdv : kBatchPixels;
+    if (rows)
+      d.kind = kBatchRows;
+    else if (p->c.depth_mode == kDepthPoly)
+      d.kind = p->one_adv ? kBatchPixelsPolyOneAdv : kBatchPixelsPoly;
+    else
+      d.kind = p->one_adv ? kBatchPixelsOneAdv : kBatchPixels;
     if (P > 0) {
       dr_plan_t tmp = *p;
       tmp.tune = t;

@@ -190,8 +190,24 @@ __device__ __forceinline__ int32_t depth_fx_exact(const GroupC &g, const StepC &
   return (int32_t)((uint32_t)s.zfx + (uint32_t)g.Q0fx + (uint32_t)rfx);
 }
 
+// The polynomial form (dr_tables.h): the group's 32 bytes read as GroupPoly.
+__device__ __forceinline__ GroupPoly as_poly(const GroupC &g) {
+  GroupPoly p;
+  memcpy(&p, &g, sizeof(p));
+  return p;
+}
+
+__device__ __forceinline__ int32_t depth_fx_poly(const GroupC &g, const StepC &s) {
+  const GroupPoly p = as_poly(g);
+  const float d = s.dz;
+  const float r = __fmaf_rn(__fmaf_rn(__fmaf_rn(p.c3, d, p.c2), d, p.c1), d, p.c0);
+  return (int32_t)((uint32_t)s.zfx + (uint32_t)p.q0fx +
+                   (uint32_t)__float_as_int(__fadd_rn(r, kRoundMagic)));
+}
+
 __device__ __forceinline__ int32_t depth_fx(const GroupC &g, const StepC &s, const Consts &c) {
-  return c.depth_series ? depth_fx_series(g, s, c) : depth_fx_exact(g, s, c);
+  if (c.depth_mode == kDepthPoly) return depth_fx_poly(g, s);
+  return c.depth_mode == kDepthSeries ? depth_fx_series(g, s, c) : depth_fx_exact(g, s, c);
 }
 
 // Two steps of one group at once with Blackwell's packed FP32 ops (each
@@ -289,9 +305,32 @@ __device__ __forceinline__ void depth_fx2_exact(const GroupC &g, const StepC &s0
   d1 = (int32_t)((uint32_t)s1.zfx + (uint32_t)g.Q0fx + (uint32_t)__float2int_rn(r1));
 }
 
+// depth_fx_poly of steps s0 and s1 of one group, operation for operation
+// (the coefficient pairs are formed by the caller once per group)
+struct Poly2 {
+  f2 c0, c1, c2, c3, magic;
+  int32_t q0fx;
+};
+__device__ __forceinline__ Poly2 poly2_of(const GroupC &g) {
+  const GroupPoly p = as_poly(g);
+  return {f2_splat(p.c0), f2_splat(p.c1), f2_splat(p.c2), f2_splat(p.c3), f2_splat(kRoundMagic),
+          p.q0fx};
+}
+__device__ __forceinline__ void depth_fx2_poly(const Poly2 &q, const StepC &s0, const StepC &s1,
+                                               int32_t &d0, int32_t &d1) {
+  const f2 d = f2_pack(s0.dz, s1.dz);
+  const f2 r = f2_add(f2_fma(f2_fma(f2_fma(q.c3, d, q.c2), d, q.c1), d, q.c0), q.magic);
+  float r0, r1;
+  f2_unpack(r, r0, r1);
+  d0 = (int32_t)((uint32_t)s0.zfx + (uint32_t)q.q0fx + (uint32_t)__float_as_int(r0));
+  d1 = (int32_t)((uint32_t)s1.zfx + (uint32_t)q.q0fx + (uint32_t)__float_as_int(r1));
+}
+
 __device__ __forceinline__ void depth_fx2(const GroupC &g, const StepC &s0, const StepC &s1,
                                           const Consts &c, int32_t &d0, int32_t &d1) {
-  if (c.depth_series)
+  if (c.depth_mode == kDepthPoly)
+    depth_fx2_poly(poly2_of(g), s0, s1, d0, d1);
+  else if (c.depth_mode == kDepthSeries)
     depth_fx2_series(g, s0, s1, c, d0, d1);
   else
     depth_fx2_exact(g, s0, s1, c, d0, d1);
@@ -747,12 +786,17 @@ __device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint1
       }
     };
     if constexpr (kFx) {
-      if (c.depth_series)
+      if (c.depth_mode == kDepthPoly) {
+        const Poly2 q = poly2_of(g);  // coefficient pairs formed once per pixel
+        fill([&q](const GroupC &, const StepC &s0, const StepC &s1, const Consts &, int32_t &d0,
+                  int32_t &d1) { depth_fx2_poly(q, s0, s1, d0, d1); });
+      } else if (c.depth_mode == kDepthSeries) {
         fill([](const GroupC &g, const StepC &s0, const StepC &s1, const Consts &c,
                 int32_t &d0, int32_t &d1) { depth_fx2_series(g, s0, s1, c, d0, d1); });
-      else
+      } else {
         fill([](const GroupC &g, const StepC &s0, const StepC &s1, const Consts &c,
                 int32_t &d0, int32_t &d1) { depth_fx2_exact(g, s0, s1, c, d0, d1); });
+      }
     } else {
       fill([](const auto &g, const auto &s0, const auto &s1, const Consts &c, pos_t &d0,
               pos_t &d1) { Geo::depth2(g, s0, s1, c, d0, d1); });
@@ -960,15 +1004,198 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks)
                                         blockIdx.x * t.tile_cols, smem, 0u);
 }
 
+// ------------------------------------------ per-pixel kernel, cubic form ---
+// The per-pixel kernel for plans whose remainder takes the polynomial form
+// (dr_tables.h): a position is three multiply-adds and a rounding, so each
+// lane computes its pixel's positions in the walk, as it reaches them,
+// instead of a phase that fills a [K][tile_cols] table first.  Shared memory
+// holds only the image tile, the step table (z_k - z_c, fixed-point z_k) and
+// the edges, so several CTAs share an SM.  Thread mapping, data span, zero
+// stores, the split of the span over the shares and the walk are those of
+// pixels_tile with FP32 geometry, and the positions are those of
+// depth_fx_poly, so the bins are bitwise the same.
+// Shared-memory layout: [0, 128) mbarrier, the image tile [Kpad][tile_cols]
+// uint16, the steps [K] of (dz bits, zfx), the bin edges [B + 1].
+template <class OutT, bool kTma, bool kOneAdv>
+__device__ __forceinline__ bool pixels_poly_tile(const CUtensorMap *tmap, const uint16_t *img,
+                                                 OutT *out, const Consts &c, const Tuning &t,
+                                                 int row, int c0, unsigned char *smem,
+                                                 uint32_t parity) {
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  uint16_t *simg = reinterpret_cast<uint16_t *>(smem + 128);
+  const int TC = t.tile_cols, K = c.K, B = c.B, G = t.bin_groups;
+  const int Kpad = t.kc * t.nchunks;
+  int2 *sstep = reinterpret_cast<int2 *>(smem + 128 + align16((size_t)Kpad * TC * 2));
+  int32_t *sedge = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(sstep) +
+                                               align16((size_t)K * sizeof(int2)));
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int SW = min(TC, 32), nslab = TC / SW, swl = __ffs(SW) - 1;  // SW: 8, 16 or 32
+  const int sl = tid & (SW - 1), grp = tid >> swl;
+  const int slab = grp % nslab, share = grp / nslab;
+  const int lc = slab * SW + sl;
+  const int ncols = min(TC, c.W - c0);
+  const bool valid = lc < ncols;
+
+  stage_tile<kTma>(tmap, img, simg, bar, c, t, row, c0);
+  for (int k = tid; k < K; k += NT) {
+    const StepC s = c.stp[k];
+    sstep[k] = make_int2(__float_as_int(s.dz), s.zfx);
+  }
+  for (int j = tid; j <= B; j += NT) sedge[j] = c.efx[j];
+  const GroupPoly gp = as_poly(c.grp[valid ? row * c.W + c0 + lc : row * c.W + c0]);
+  __syncthreads();  // also makes the mbarrier initialisation visible
+  // position of step k: depth_fx_poly, operation for operation
+  auto pos = [&](int k) {
+    const int2 st = sstep[k];
+    const float d = __int_as_float(st.x);
+    const float r = __fmaf_rn(__fmaf_rn(__fmaf_rn(gp.c3, d, gp.c2), d, gp.c1), d, gp.c0);
+    return (int32_t)((uint32_t)st.y + (uint32_t)gp.q0fx +
+                     (uint32_t)__float_as_int(__fadd_rn(r, kRoundMagic)));
+  };
+  auto count_prefix = [](float guess, int n, auto below) {
+    int g = (int)fminf(fmaxf(guess, 0.f), (float)n);
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+      const bool lo_ok = g == 0 || below(g - 1);
+      const bool hi_ok = g == n || !below(g);
+      if (lo_ok && hi_ok) return g;
+      g += lo_ok ? 1 : -1;
+    }
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (below(mid)) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+  };
+  const int32_t tfirst = pos(0), tlast = pos(K - 1);
+  const int32_t e0 = sedge[0];
+  const float bins_per_pos = (float)B / ((float)sedge[B] - (float)e0);
+  const int32_t lo_d = group_min(valid ? tfirst : sedge[B], SW);
+  const int32_t hi_d = group_max(valid ? tlast : e0, SW);
+  const int n_le = count_prefix(((float)lo_d - (float)e0) * bins_per_pos + 1.f, B + 1,
+                                [&](int i) { return !(sedge[i] > lo_d); });
+  const int n_lt = count_prefix(((float)hi_d - (float)e0) * bins_per_pos + 1.f, B + 1,
+                                [&](int i) { return sedge[i] < hi_d; });
+  const int jlo = min(max(n_le - 1, 0), B);
+  const int2 sp = make_int2(jlo, max(min(n_lt, B), jlo));
+  if constexpr (kTma) {
+    const bool late = !mbar_wait_bounded(bar, parity, c.err);
+    if (__syncthreads_or(late)) return false;
+  }
+  const float sign = c.out_sign, zero = __fmul_rn(sign, 0.f);
+  const size_t plane = (size_t)c.H * c.W;
+  const bool acc = c.accumulate != 0;
+  if (!acc) {  // the bins outside the span: zeros, as in pixels_tile
+    constexpr int kPer = 16 / sizeof(OutT);
+    const int kVec = SW / kPer, kvl = __ffs(kVec) - 1;
+    const int nz = B - (sp.y - sp.x);
+    OutT *const os = out + (size_t)row * c.W + c0 + slab * SW;
+    if (slab * SW + SW <= ncols && c.W % kPer == 0 && ((uintptr_t)out & 15) == 0) {
+      const uint4 zv = zero_bits<OutT>(zero);
+      for (int i = share * SW + sl; i < nz * kVec; i += G * SW) {
+        const int z = i >> kvl, part = i & (kVec - 1);
+        const int j = z < sp.x ? z : z - sp.x + sp.y;
+        st_cs_u4(os + (size_t)j * plane + part * kPer, zv);
+      }
+    } else if (valid) {
+      for (int z = share; z < nz; z += G) {
+        const int j = z < sp.x ? z : z - sp.x + sp.y;
+        st_cs(os + (size_t)j * plane + sl, zero);
+      }
+    }
+  }
+  if (!valid) return true;
+  const int nd = sp.y - sp.x;
+  const int jb = sp.x + (int)((long long)nd * share / G);
+  const int je = sp.x + (int)((long long)nd * (share + 1) / G);
+  if (jb >= je) return true;
+  const bool rev = c.reverse != 0;
+  const uint16_t *ip = simg + (rev ? (K - 1) * TC : 0) + lc;
+  const int istep = rev ? -TC : TC;
+  int32_t eb = sedge[jb];
+  const int n_below = count_prefix(
+      ((float)eb - (float)tfirst) * ((float)(K - 1) / ((float)tlast - (float)tfirst)) + 1.f, K,
+      [&](int i) { return pos(i) < eb; });
+  const int k = min(max(n_below - 1, 0), K - 2);
+  // walk state: t0 = t_k, t1 = t_{k+1} (step k1 = k + 1), the image of step
+  // k + 1 at ipn, base = I_0 - I_k, dI = I_k - I_{k+1}
+  int k1 = k + 1;
+  int32_t t0 = pos(k), t1 = pos(k1);
+  const float I0 = biased(ip[0]);
+  const uint16_t *ipn = ip + k1 * istep;
+  float Ik1 = biased(*ipn);
+  const float Ik = biased(ipn[-istep]);
+  float base = __fsub_rn(I0, Ik), dI = __fsub_rn(Ik, Ik1);
+  float inv = GeoFx::inv_len(t0, t1);
+  auto advance = [&]() {
+    t0 = t1;
+    t1 = pos(++k1);
+    ipn += istep;
+    const float In = biased(*ipn);
+    base = __fsub_rn(I0, Ik1);
+    dI = __fsub_rn(Ik1, In);
+    Ik1 = In;
+    inv = GeoFx::inv_len(t0, t1);
+  };
+  auto F_at = [&](int32_t e) {
+    const int32_t ec = min(e, tlast);
+    if (t1 < ec) advance();
+    if constexpr (!kOneAdv) {
+      while (t1 < ec) advance();
+    }
+    return __fmaf_rn(__fmul_rn(cvt23(max(ec, t0) - t0), inv), dI, base);
+  };
+  OutT *o = out + (size_t)row * c.W + c0 + lc + (size_t)jb * plane;
+  float Fp = F_at(eb);
+  if (acc) {
+    for (int j = jb; j < je; ++j, o += plane) {
+      const int32_t e1 = sedge[j + 1];
+      const float F = F_at(e1);
+      const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
+      if (e1 > tfirst && eb < tlast) st_cs(o, __fadd_rn(out_load(o), v));
+      Fp = F;
+      eb = e1;
+    }
+  } else {
+#pragma unroll 4
+    for (int j = jb; j < je; ++j, o += plane) {
+      const float F = F_at(sedge[j + 1]);
+      st_cs(o, __fmul_rn(sign, __fsub_rn(F, Fp)));
+      Fp = F;
+    }
+  }
+  return true;
+}
+
+template <class OutT, bool kTma, bool kOneAdv>
+__global__ void __launch_bounds__(512, 3)
+    pixels_poly_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *__restrict__ img,
+                       OutT *__restrict__ out, const Consts c, const Tuning t) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if constexpr (kTma) {
+    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
+  }
+  pixels_poly_tile<OutT, kTma, kOneAdv>(&tmap, img, out, c, t, blockIdx.y,
+                                        blockIdx.x * t.tile_cols, smem, 0u);
+}
+
 // ------------------------------------------------- persistent batch kernel ---
 // Many scans (each with its own plan tables, tensor map and tile shape) in
 // one launch: every CTA takes (scan, row, tile) work items from a device
 // counter until none are left.  Items are numbered scan by scan in the order
 // of the descriptor array.
 
-// Work-item kinds: a rows tile, or a per-pixel tile (with at most one step
-// advance per bin, or the general walk).
-enum : int { kBatchRows = 0, kBatchPixelsOneAdv = 1, kBatchPixels = 2 };
+// Work-item kinds: a rows tile, or a per-pixel tile (depth table or the
+// polynomial form; with at most one step advance per bin, or the general
+// walk).
+enum : int {
+  kBatchRows = 0,
+  kBatchPixelsOneAdv = 1,
+  kBatchPixels = 2,
+  kBatchPixelsPolyOneAdv = 3,
+  kBatchPixelsPoly = 4
+};
 
 struct BatchScan {
   CUtensorMap tmap;        // [K][rows][cols] images, box [kc][1][tile_cols]
@@ -1013,6 +1240,12 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(const BatchScan *__restri
     bool ok;
     if (S.kind == kBatchRows)
       ok = rows_tile<GeoFx, OutT, true, 4>(&S.tmap, S.img, o, S.c, S.t, row, c0, smem, parity);
+    else if (S.kind == kBatchPixelsPolyOneAdv)
+      ok = pixels_poly_tile<OutT, true, true>(&S.tmap, S.img, o, S.c, S.t, row, c0, smem,
+                                              parity);
+    else if (S.kind == kBatchPixelsPoly)
+      ok = pixels_poly_tile<OutT, true, false>(&S.tmap, S.img, o, S.c, S.t, row, c0, smem,
+                                               parity);
     else if (S.kind == kBatchPixelsOneAdv)
       ok = pixels_tile<GeoFx, OutT, true, true>(&S.tmap, S.img, o, S.c, S.t, row, c0, smem,
                                                 parity);

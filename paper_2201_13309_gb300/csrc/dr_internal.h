@@ -26,6 +26,7 @@ struct dr_plan {
   int threads, smem_bytes;
   size_t device_bytes;
   void *dev_block;         // single device allocation holding every table
+  int device = 0;          // the device it lives on
   // what the plan-time check of every (group, step) found (FP32 geometry of
   // the running-sum kernels): groups checked, largest step and largest
   // distance from FP64 in grid units (-1: not checked), and whether every
@@ -64,6 +65,8 @@ constexpr int kSmemPerCtaMax = 227 * 1024;   // opt-in maximum per CTA
 // Shared-memory bytes of one rows / pixels tile (layouts in dr_device.cuh).
 int rows_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64);
 int pixels_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64);
+// The per-pixel kernel of the polynomial form (no depth table).
+int pixels_poly_smem_bytes(int K, int Kpad, int B, int tile_cols);
 // Interval kernel: pixels per CTA (one warp each), and the shared-memory
 // bytes of one tile: mbarrier, image tile [Kpad][8] uint16, depths [K][8],
 // edges [B + 1], int64 accumulators [window][8] (dr_intervals.cuh).
@@ -82,7 +85,19 @@ dr_status allow_smem(const void *fn);
 dr_status make_tensor_map(const dr_plan_t *p, const uint16_t *img, CUtensorMap *tm);
 // Run check_kernel over the plan's ngroups groups into the device record
 // d_res and copy the result to *h_res; synchronous.
-dr_status run_plan_check(const dr_plan_t *p, int ngroups, PlanCheck *d_res, PlanCheck *h_res);
+dr_status run_plan_check(const dr_plan_t *p, int ngroups, bool monotone, PlanCheck *d_res,
+                         PlanCheck *h_res);
+// Inputs of the per-group constants (groups_kernel): affine pixel
+// coordinates in the projected frame, the wire's y0 and signed radius, the
+// grid scale, the z range of the path (centre, half width) and the form of
+// the remainder.
+struct GroupsParams {
+  double Y00, Yr, Yc, Z00, Zr, Zc, y0, sR, scale, zc, zh;
+  long long ngroups;
+  int W, rows_shared, mode, pad;
+};
+// Compute every group's GroupC / GroupD on the device; synchronous.
+dr_status run_groups(const GroupsParams &q, GroupC *gc, GroupD *gd);
 // Build the plan's per-row (k, f) tables into tab (H rows of c.tab_stride
 // entries) on the device; synchronous.
 dr_status build_plan_tables(const dr_plan_t *p, int2 *tab);

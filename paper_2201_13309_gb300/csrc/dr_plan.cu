@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "dr_internal.h"
@@ -66,6 +67,45 @@ double solve_t(double Y, double Z, double y0, double sR, double D, double L0,
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Device memory of plans: a stream-ordered pool per device (allocation and
+// release on a library stream), so that building and destroying plans while
+// other work runs neither waits for the device nor makes it wait, as
+// cudaMalloc / cudaFree can.  The pool keeps up to 4 GiB of released blocks
+// for later plans.
+struct PlanMemory {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t stream = nullptr;
+  bool ok = false;
+};
+std::mutex g_plan_mem_mu;
+PlanMemory g_plan_mem[64];
+
+dr_status plan_memory(int dev, PlanMemory **out) {
+  if (dev < 0 || dev >= 64) {
+    set_error("dr_plan: device %d out of range", dev);
+    return DR_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_plan_mem_mu);
+  PlanMemory &m = g_plan_mem[dev];
+  if (!m.ok) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaError_t e = cudaMemPoolCreate(&m.pool, &props);
+    if (e == cudaSuccess) {
+      uint64_t keep = uint64_t(4) << 30;
+      e = cudaMemPoolSetAttribute(m.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m.stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail("dr_plan: memory pool", e);
+    m.ok = true;
+  }
+  *out = &m;
+  return DR_OK;
+}
+
 }  // namespace
 }  // namespace dr
 
@@ -92,6 +132,14 @@ int pixels_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64) {
   s += align_up((size_t)Kpad * tile_cols * 2, 16);                 // image tile
   s += align_up((size_t)K * tile_cols * (f64 ? 8 : 4), 16);        // depth positions
   s += align_up((size_t)(B + 1) * (f64 ? 8 : 4), 16);              // edges
+  return (int)s;
+}
+
+int pixels_poly_smem_bytes(int K, int Kpad, int B, int tile_cols) {
+  size_t s = 128;
+  s += align_up((size_t)Kpad * tile_cols * 2, 16);                 // image tile
+  s += align_up((size_t)K * 8, 16);                                // steps (dz, zfx)
+  s += align_up((size_t)(B + 1) * 4, 16);                          // edges
   return (int)s;
 }
 
@@ -128,12 +176,15 @@ void choose_chunks(int K, int tile_cols, int *kc, int *nchunks) {
 // chosen by the whole scan's travel), for the runs of a composite plan whose
 // own travel may point the other way.
 // shift_cap bounds the fixed-point scale (a retry after the check found a
-// step too long for it); allow_series = false forces the exact form of dL.
+// step too long for it or positions off the FP64 solution); max_mode bounds
+// the form of the FP32 remainder (a retry after the check found a cheaper
+// form not accurate enough).
 static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wires, int32_t K,
                           const double *edges, int32_t B, const dr_plan_options *opt_in,
                           int side, dr_plan_t **out, int shift_cap = 40,
-                          bool allow_series = true) {
+                          int max_mode = kDepthPoly) {
   if (out) *out = nullptr;
+  if (opt_in && opt_in->depth_form > 0) max_mode = std::min(max_mode, opt_in->depth_form - 1);
   if (!g || !wires || !edges || !out) {
     set_error("dr_plan: null argument");
     return DR_ERR_INVALID_ARG;
@@ -155,7 +206,7 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   }
   if ((opt.out_dtype != DR_OUT_F32 && opt.out_dtype != DR_OUT_BF16) ||
       (opt.geom_precision != DR_GEOM_FP32 && opt.geom_precision != DR_GEOM_FP64) ||
-      opt.tile_cols < 0 || opt.bin_groups < 0) {
+      opt.tile_cols < 0 || opt.bin_groups < 0 || opt.depth_form < 0 || opt.depth_form > 3) {
     set_error("dr_plan: bad options");
     return DR_ERR_INVALID_ARG;
   }
@@ -253,58 +304,61 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   if (opt.force_pixels) rows_shared = false;
   if (W == 0 || H == 0) rows_shared = true;
 
-  const int G = rows_shared ? H : (int)P;
+  const long long G = rows_shared ? H : P;
   if (!rows_shared && P > (1LL << 31) / 2) {
     set_error("dr_plan: too many pixels for the per-pixel kernel");
     return DR_ERR_UNSUPPORTED;
   }
-  std::vector<Group64> grp(G);
-  for (int i = 0; i < G; ++i) {
-    double r = rows_shared ? i : i / W, c = rows_shared ? 0 : i % W;
+  auto group_at = [&](double r, double c) {
     Group64 q;
     q.Y = Y00 + r * Yr + c * Yc;
     q.Z = Z00 + r * Zr + c * Zc;
     q.D = q.Y - y0;
     q.L0 = std::sqrt(q.Y * q.Y + q.Z * q.Z);
     q.Q0 = (-y0 * q.Z + sR * q.L0) / q.D;
-    grp[i] = q;
-  }
+    return q;
+  };
 
   // Steps in processing order (increasing depth).
   std::vector<double> zp(K), ep(K);
+  double zlo = 1e300, zhi = -1e300;
   for (int k = 0; k < K; ++k) {
     int src = reverse ? K - 1 - k : k;
     zp[k] = zk[src];
     ep[k] = yk[src] - y0;
+    zlo = std::min(zlo, zp[k]);
+    zhi = std::max(zhi, zp[k]);
   }
 
-  // ---- FP64 depth sequences: monotonicity, range, smallest step ----
-  // Row groups: every (group, step), and a sequence that does not increase
-  // stops the plan here.  Pixel groups: every pixel at the first and last
-  // step (the range) and a sub-grid of pixels at every step, for the
-  // estimates of the range, step sizes and remainder that set the
-  // fixed-point scale; whether every pixel's sequence increases is decided
-  // by the check of every (pixel, step) on the device after the upload.
-  double tmin = 1e300, tmax = -1e300, minstep = 1e300, maxstep = 0.0, remmax = 0.0;
-  auto check_group = [&](const Group64 &q, bool all_steps, int *bad_k) -> bool {
+  // ---- FP64 estimates on a sample of groups ----
+  // The sample sets the fixed-point scale and the form of the remainder; the
+  // device check after the upload computes every (group, step) as the
+  // kernels will and decides whether the plan stands.  Rows: every 8th row
+  // and the last; pixels: every 64th row and column and the last ones (all
+  // four corners).  A sampled sequence that does not increase ends the plan
+  // here.
+  double tmin = 1e300, tmax = -1e300, minstep = 1e300, maxstep = 0.0, remmax = 0.0, qmax = 0.0;
+  long long bad_r = -1, bad_c = -1;
+  int bad_k = -1;
+  auto sample = [&](double r, double c) {
+    const Group64 q = group_at(r, c);
+    qmax = std::max(qmax, std::fabs(q.Q0));
     double prev = 0;
     for (int k = 0; k < K; ++k) {
-      if (!all_steps && k != 0 && k != K - 1) continue;
-      double t = solve_t(q.Y, q.Z, y0, sR, q.D, q.L0, q.Q0, zp[k], ep[k]);
+      const double t = solve_t(q.Y, q.Z, y0, sR, q.D, q.L0, q.Q0, zp[k], ep[k]);
       tmin = std::min(tmin, t);
       tmax = std::max(tmax, t);
       remmax = std::max(remmax, std::fabs(t - zp[k] - q.Q0));
-      if (all_steps && k > 0) {
-        double st = t - prev;
+      if (k > 0) {
+        const double st = t - prev;
         if (intervals) {  // any order: only the smallest nonzero step is kept
           if (st != 0) minstep = std::min(minstep, std::fabs(st));
         } else if (!(st > 0)) {
-          if (!rows_shared) {  // left to the device check of every pixel
-            prev = t;
-            continue;
+          if (bad_k < 0) {
+            bad_r = (long long)r;
+            bad_c = (long long)c;
+            bad_k = k;
           }
-          *bad_k = k;
-          return false;
         } else {
           minstep = std::min(minstep, st);
           maxstep = std::max(maxstep, st);
@@ -312,26 +366,25 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
       }
       prev = t;
     }
-    return true;
   };
   if (P > 0) {
-    int bad_k = -1;
-    if (rows_shared) {
-      for (int i = 0; i < G; ++i)
-        if (!check_group(grp[i], true, &bad_k)) {
-          set_error("dr_plan: depth of row %d not monotone at step %d", i, bad_k);
-          return DR_ERR_NONMONOTONIC;
-        }
-    } else {
-      const int stride = 16;
-      for (int r = 0; r < H; ++r)
-        for (int c = 0; c < W; ++c) {
-          bool sub = (r % stride == 0 || r == H - 1) && (c % stride == 0 || c == W - 1);
-          if (!check_group(grp[(size_t)r * W + c], sub, &bad_k)) {
-            set_error("dr_plan: depth of pixel (%d,%d) not monotone at step %d", r, c, bad_k);
-            return DR_ERR_NONMONOTONIC;
-          }
-        }
+    auto picks = [](long long n, long long stride) {  // 0, stride, 2 stride, ..., n - 1
+      std::vector<long long> v;
+      for (long long i = 0; i < n; i += stride) v.push_back(i);
+      if (v.back() != n - 1) v.push_back(n - 1);
+      return v;
+    };
+    const std::vector<long long> prow = picks(H, rows_shared ? 8 : 64);
+    const std::vector<long long> pcol = rows_shared ? std::vector<long long>{0} : picks(W, 64);
+    for (long long r : prow)
+      for (long long c : pcol) sample((double)r, (double)c);
+    if (bad_k >= 0) {
+      if (rows_shared)
+        set_error("dr_plan: depth of row %lld not monotone at step %d", bad_r, bad_k);
+      else
+        set_error("dr_plan: depth of pixel (%lld,%lld) not monotone at step %d", bad_r, bad_c,
+                  bad_k);
+      return DR_ERR_NONMONOTONIC;
     }
   }
   if (P == 0) {
@@ -341,18 +394,23 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   }
 
   // ---- fixed-point scale ----
+  // positions (relative to the origin) get a budget of 2^29 grid units, four
+  // times below the int32 limit, which covers any range the sample missed;
+  // the device check measures the true range and the distance of every
+  // position from FP64, and a plan whose positions went wrong is rebuilt on
+  // a coarser grid
   double lo = std::min(tmin, edges[0] * nb), hi = std::max(tmax, edges[B] * nb);
   double origin = 0.5 * (lo + hi);
   double mag = 0.5 * (hi - lo) * 1.001 + 1e-9;
   for (int k = 0; k < K; ++k) mag = std::max(mag, std::fabs(zp[k] - origin));
-  for (int i = 0; i < G; ++i) mag = std::max(mag, std::fabs(grp[i].Q0));
+  mag = std::max(mag, qmax * 1.05);
   mag = std::max(mag, remmax * 1.5);
   int shift = (int)std::floor(std::log2((double)(1 << 29) / mag));
   shift = std::min(shift, shift_cap);
   // FP32 geometry of the running-sum kernels: every step must stay below
   // 2^23 grid units (exact conversion of position differences); the check
   // below confirms it for every (group, step) and retries with a smaller
-  // scale if a step the host did not sample is longer
+  // scale if a step the sample missed is longer
   const bool fx_walk = !intervals && opt.geom_precision == DR_GEOM_FP32;
   if (fx_walk && maxstep > 0.0)
     shift = std::min(shift, (int)std::floor(std::log2(0.9 * kMaxStepUnits / maxstep)));
@@ -371,13 +429,14 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
     return DR_ERR_UNSUPPORTED;
   }
 
-  // ---- series form of dL (dr_tables.h) ----
-  // Bound of the first dropped term, n / (2 L0) * 5/64 * x^3 / (1 - x), over
+  // ---- form of the FP32 remainder (dr_tables.h) ----
+  // Polynomial: a wire at one distance from the beam (eta = 0) and a
+  // remainder that rounds by the 1.5 * 2^23 construction.  Series: the
+  // bound of its first dropped term, n / (2 L0) * 5/64 * x^3 / (1 - x), over
   // the ROI (|t| <= T, |Z| <= Zmax, L0 >= Y >= Ymin), carried into the
-  // remainder (times R / D) in grid units; the remainder itself must round
-  // by the 1.5 * 2^23 construction (|rem * 2^shift| < 2^22).
-  bool series = false;
-  if (fx_walk && allow_series && !has_eta && P > 0) {
+  // remainder (times R / D) in grid units, below 0.01.  Otherwise exact.
+  int mode = kDepthExact;
+  if (fx_walk && !has_eta && P > 0 && remmax * scale < (double)(1 << 20)) {
     double Zmax = 0.0, Ymin = 1e300;
     for (int cr = 0; cr < 4; ++cr) {
       const double r = (cr & 1) ? H - 1 : 0, cc = (cr & 2) ? W - 1 : 0;
@@ -386,35 +445,26 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
     }
     const double T = std::max(std::fabs(tmin), std::fabs(tmax)) * 1.01 + 1e-6;
     const double n = T * (T + 2.0 * Zmax), x = n / (Ymin * Ymin);
+    bool series_ok = false;
     if (Ymin > y0 && x < 0.5) {
       const double drop = n / (2.0 * Ymin) * (5.0 / 64.0) * x * x * x / (1.0 - x);
-      const double units = R / (Ymin - y0) * drop * scale;
-      series = units < 0.01 && remmax * scale < (double)(1 << 21);
+      series_ok = R / (Ymin - y0) * drop * scale < 0.01;
     }
+    if (max_mode >= kDepthPoly)
+      mode = kDepthPoly;
+    else if (max_mode >= kDepthSeries && series_ok)
+      mode = kDepthSeries;
   }
+  const double zc = 0.5 * (zlo + zhi), zh = 0.5 * (zhi - zlo);
 
-  // ---- host tables ----
-  std::vector<GroupC> gc(G);
-  std::vector<GroupD> gd(G);
-  for (int i = 0; i < G; ++i) {
-    const Group64 &q = grp[i];
-    gc[i].Z = (float)q.Z;
-    gc[i].Y2 = (float)(q.Y * q.Y);
-    gc[i].L0 = (float)q.L0;
-    gc[i].invD = (float)(1.0 / q.D);
-    gc[i].D = (float)q.D;
-    gc[i].Q0f = (float)q.Q0;
-    gc[i].Q0fx = (int32_t)std::llround(q.Q0 * scale);
-    gc[i].invL0 = (float)(1.0 / q.L0);
-    gd[i] = {q.Z, q.Y * q.Y, q.L0, q.D, q.Q0};
-  }
+  // ---- host tables (steps, edges; the groups are computed on the device) ----
   std::vector<StepC> sc(K);
   std::vector<StepD> sd(K);
   for (int k = 0; k < K; ++k) {
     sc[k].zf = (float)zp[k];
     sc[k].eta = (float)ep[k];
     sc[k].zfx = (int32_t)std::llround((zp[k] - origin) * scale);
-    sc[k].pad = 0.f;
+    sc[k].dz = (float)(zp[k] - zc);
     sd[k] = {zp[k], ep[k]};
   }
   std::vector<int32_t> efx(B + 1);
@@ -451,8 +501,9 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   auto smem_for = [&](int tc) {
     int kc, n;
     choose_chunks(K, tc, &kc, &n);
-    return rows_shared ? rows_smem_bytes(K, kc * n, B, tc, f64)
-                       : pixels_smem_bytes(K, kc * n, B, tc, f64);
+    if (rows_shared) return rows_smem_bytes(K, kc * n, B, tc, f64);
+    return mode == kDepthPoly ? pixels_poly_smem_bytes(K, kc * n, B, tc)
+                              : pixels_smem_bytes(K, kc * n, B, tc, f64);
   };
   if (intervals) {
     // 8 pixels x all steps per CTA, one warp per pixel; bins in windows of
@@ -550,17 +601,20 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   p->tune = t;
 
   // ---- device upload (one allocation) ----
+  // the small tables first (uploaded from the host), then the per-group
+  // constants (computed on the device) and the row tables
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = align_up(off, 256);
     off = o + bytes;
     return o;
   };
-  size_t o_gc = take(sizeof(GroupC) * G), o_sc = take(sizeof(StepC) * K);
-  size_t o_efx = take(sizeof(int32_t) * (B + 1)), o_gd = take(sizeof(GroupD) * G);
+  size_t o_sc = take(sizeof(StepC) * K), o_efx = take(sizeof(int32_t) * (B + 1));
   size_t o_sd = take(sizeof(StepD) * K), o_e64 = take(sizeof(double) * (B + 1));
   size_t o_err = take(sizeof(int32_t) * 4);
   size_t o_chk = take(sizeof(PlanCheck));
+  const size_t host_bytes = align_up(off, 256);
+  size_t o_gc = take(sizeof(GroupC) * (size_t)G), o_gd = take(sizeof(GroupD) * (size_t)G);
   // per-row (k, f) tables, built once on the device below (rows kernel only;
   // above 1 GiB the tiles build their own)
   const int tab_stride = row_table_entries(B);
@@ -570,32 +624,65 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   size_t o_tab = row_tables ? take(tab_bytes) : 0;
   size_t total = align_up(off, 256);
   void *blk = nullptr;
-  cudaError_t ce = cudaMalloc(&blk, total);
+  PlanMemory *pm = nullptr;
+  cudaError_t ce = cudaGetDevice(&p->device);
+  if (ce != cudaSuccess) {
+    delete p;
+    return cuda_fail("dr_plan: cudaGetDevice", ce);
+  }
+  dr_status ms = plan_memory(p->device, &pm);
+  if (ms != DR_OK) {
+    delete p;
+    return ms;
+  }
+  ce = cudaMallocFromPoolAsync(&blk, total, pm->pool, pm->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(pm->stream);
   if (ce != cudaSuccess) {
     delete p;
     if (ce == cudaErrorMemoryAllocation) {
       cudaGetLastError();
-      set_error("dr_plan: cudaMalloc of %zu bytes failed", total);
+      set_error("dr_plan: device allocation of %zu bytes failed", total);
       return DR_ERR_OOM;
     }
-    return cuda_fail("dr_plan: cudaMalloc", ce);
+    return cuda_fail("dr_plan: device allocation", ce);
   }
-  std::vector<char> host(total, 0);
-  std::memcpy(host.data() + o_gc, gc.data(), sizeof(GroupC) * G);
+  std::vector<char> host(host_bytes, 0);
   std::memcpy(host.data() + o_sc, sc.data(), sizeof(StepC) * K);
   std::memcpy(host.data() + o_efx, efx.data(), sizeof(int32_t) * (B + 1));
-  std::memcpy(host.data() + o_gd, gd.data(), sizeof(GroupD) * G);
   std::memcpy(host.data() + o_sd, sd.data(), sizeof(StepD) * K);
   std::memcpy(host.data() + o_e64, e64.data(), sizeof(double) * (B + 1));
-  ce = cudaMemcpy(blk, host.data(), total, cudaMemcpyHostToDevice);
+  ce = cudaMemcpy(blk, host.data(), host_bytes, cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) {
-    cudaFree(blk);
+    cudaFreeAsync(blk, pm->stream);
     delete p;
     return cuda_fail("dr_plan: upload", ce);
   }
   char *b = (char *)blk;
   p->dev_block = blk;
   p->device_bytes = total;
+  GroupsParams gq;
+  std::memset(&gq, 0, sizeof(gq));
+  gq.Y00 = Y00;
+  gq.Yr = Yr;
+  gq.Yc = Yc;
+  gq.Z00 = Z00;
+  gq.Zr = Zr;
+  gq.Zc = Zc;
+  gq.y0 = y0;
+  gq.sR = sR;
+  gq.scale = scale;
+  gq.zc = zc;
+  gq.zh = zh;
+  gq.ngroups = G;
+  gq.W = W;
+  gq.rows_shared = rows_shared ? 1 : 0;
+  gq.mode = mode;
+  dr_status gs = run_groups(gq, reinterpret_cast<GroupC *>(b + o_gc),
+                            reinterpret_cast<GroupD *>(b + o_gd));
+  if (gs != DR_OK) {
+    dr_plan_destroy(p);
+    return gs;
+  }
   Consts &c = p->c;
   c.grp = (const GroupC *)(b + o_gc);
   c.stp = (const StepC *)(b + o_sc);
@@ -621,15 +708,18 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   c.out_sign = (float)((g->edge == DR_EDGE_LEADING ? 1.0 : -1.0) * (reverse ? -1.0 : 1.0));
   c.tab = nullptr;
   c.tab_stride = tab_stride;
-  c.depth_series = series ? 1 : 0;
+  c.depth_mode = mode;
   p->checked_groups = 0;
   p->max_dev_units = -1;
   p->max_step_units = 0;
   p->one_adv = 0;
-  if (fx_walk && P > 0) {
-    // every (group, step) as the kernels compute it, against FP64
+  if (P > 0) {
+    // every (group, step) as the kernels compute it (and, for FP32
+    // geometry, against FP64): order for the running-sum kernels, range and
+    // accuracy for all
     PlanCheck res;
-    dr_status st = run_plan_check(p, G, reinterpret_cast<PlanCheck *>(b + o_chk), &res);
+    dr_status st =
+        run_plan_check(p, (int)G, !intervals, reinterpret_cast<PlanCheck *>(b + o_chk), &res);
     if (st != DR_OK) {
       dr_plan_destroy(p);
       return st;
@@ -638,12 +728,13 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
       const long long gi = (long long)(res.bad >> 32);
       const int k = (int)(res.bad & 0xffffffffu);
       dr_plan_destroy(p);
-      if (res.max_step >= kMaxStepUnits && res.min_step >= kMinStepUnits && shift > 12)
+      if (fx_walk && res.max_step >= kMaxStepUnits && res.min_step >= kMinStepUnits &&
+          shift > 12)
         return plan_one(intervals, g, wires, K, edges, B, opt_in, side, out, shift - 1,
-                        allow_series);
+                        max_mode);
       const long long r = rows_shared ? gi : gi / std::max(W, 1);
       const long long cc = rows_shared ? 0 : gi % std::max(W, 1);
-      if (res.min_step <= 0) {
+      if (!fx_walk || res.min_step <= 0) {
         set_error("dr_plan: depth of %s (%lld,%lld) not increasing at step %d",
                   rows_shared ? "row" : "pixel", r, cc, k);
         return DR_ERR_NONMONOTONIC;
@@ -652,17 +743,36 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
                 "fixed-point grid's range", rows_shared ? "row" : "pixel", r, cc, k);
       return DR_ERR_UNSUPPORTED;
     }
-    if (series && res.max_dev > 4) {  // the series is not good enough here
-      dr_plan_destroy(p);
-      return plan_one(intervals, g, wires, K, edges, B, opt_in, side, out, shift_cap, false);
+    if (!f64) {
+      if (mode != kDepthExact && res.max_dev > 4) {  // the cheaper form is not good enough
+        dr_plan_destroy(p);
+        return plan_one(intervals, g, wires, K, edges, B, opt_in, side, out, shift_cap,
+                        mode - 1);
+      }
+      if (res.max_dev > 64) {  // positions off the FP64 solution: a coarser grid
+        dr_plan_destroy(p);
+        if (shift <= 12) {
+          set_error("dr_plan: FP32 depth positions off the FP64 solution by %d grid units",
+                    res.max_dev);
+          return DR_ERR_UNSUPPORTED;
+        }
+        return plan_one(intervals, g, wires, K, edges, B, opt_in, side, out, shift - 1,
+                        max_mode);
+      }
+      p->max_dev_units = res.max_dev;
     }
     p->checked_groups = G;
-    p->max_dev_units = res.max_dev;
-    p->max_step_units = res.max_step;
-    p->min_step = (double)res.min_step / scale / nb;
-    long long maxbin = 0;
-    for (int j = 0; j < B; ++j) maxbin = std::max(maxbin, (long long)efx[j + 1] - efx[j]);
-    p->one_adv = res.min_step >= maxbin ? 1 : 0;
+    p->depth_min = ((double)res.tmin / scale + origin) / nb;
+    p->depth_max = ((double)res.tmax / scale + origin) / nb;
+    if (!intervals) {
+      p->max_step_units = res.max_step;
+      p->min_step = (double)res.min_step / scale / nb;
+    }
+    if (fx_walk) {
+      long long maxbin = 0;
+      for (int j = 0; j < B; ++j) maxbin = std::max(maxbin, (long long)efx[j + 1] - efx[j]);
+      p->one_adv = res.min_step >= maxbin ? 1 : 0;
+    }
   }
   if (row_tables) {
     dr_status st = build_plan_tables(p, reinterpret_cast<int2 *>(b + o_tab));
@@ -825,7 +935,11 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t 
 extern "C" void dr_plan_destroy(dr_plan_t *p) {
   if (!p) return;
   for (dr_plan_t *q : p->parts) dr_plan_destroy(q);
-  if (p->dev_block) cudaFree(p->dev_block);
+  if (p->dev_block) {
+    // stream-ordered release into the plan pool (no wait for the device)
+    PlanMemory *pm = nullptr;
+    if (plan_memory(p->device, &pm) == DR_OK) cudaFreeAsync(p->dev_block, pm->stream);
+  }
   delete p;
 }
 
@@ -862,7 +976,7 @@ extern "C" dr_status dr_plan_get_info(const dr_plan_t *p, dr_plan_info *info) {
   const double unit = std::ldexp(1.0, -p->shift) / (p->nb > 0 ? p->nb : 1.0);
   info->max_step = p->max_step_units * unit;
   info->depth_err = p->max_dev_units >= 0 ? p->max_dev_units * unit : -1.0;
-  info->depth_series = p->c.depth_series;
+  info->depth_form = p->c.depth_mode;
   info->one_step_per_bin = p->one_adv;
   info->checked_groups = p->checked_groups;
   info->device_bytes = p->device_bytes;

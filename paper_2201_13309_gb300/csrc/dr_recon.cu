@@ -38,41 +38,62 @@
 
 namespace dr {
 
-// Plan-time check of every (group, step) of an FP32-geometry plan: one
-// thread per group computes the K depth positions exactly as the kernels do
-// and the FP64 solution of the same geometry, and records (PlanCheck) the
-// first group whose positions are not strictly increasing with steps in
-// [kMinStepUnits, kMaxStepUnits), the smallest and largest step, and the
-// largest distance from the FP64 solution, in grid units.  res must hold
-// bad = ~0, min_step = INT32_MAX, max_step = max_dev = 0 before the launch.
-__global__ void __launch_bounds__(256) check_kernel(const Consts c, int ngroups,
+// Plan-time check of every (group, step): one thread per group computes
+// the K depth positions exactly as the kernels do (FP32 geometry: the
+// plan's form of the remainder on its fixed-point grid; FP64 geometry: the
+// FP64 depths) and records (PlanCheck) the first group whose positions are
+// not strictly increasing with steps in [kMinStepUnits, kMaxStepUnits)
+// (FP64: not increasing), the smallest and largest step, the range of the
+// positions and, for FP32 geometry, the largest distance from the FP64
+// solution, all in grid units.  monotone = 0 records the range and the
+// distance only (the interval kernel takes any order).  res must hold
+// bad = ~0, min_step = tmin = INT32_MAX, max_step = tmax = INT32_MIN and
+// max_dev = 0 before the launch.
+template <bool kF64>
+__global__ void __launch_bounds__(256) check_kernel(const Consts c, int ngroups, int monotone,
                                                    PlanCheck *res) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int32_t lmin = 0x7fffffff, lmax = 0, ldev = 0;
+  int32_t lmin = 0x7fffffff, lmax = (int32_t)0x80000000, ldev = 0;
+  int32_t tlo = 0x7fffffff, thi = (int32_t)0x80000000;
   unsigned long long bad = ~0ull;
   if (i < ngroups) {
-    const GroupC g = c.grp[i];
     const GroupD gd = c.grp64[i];
     const double scale = (double)c.scale;
+    auto clamp32 = [](double v) {
+      return (int32_t)fmin(fmax(rint(v), -2147483648.0), 2147483647.0);
+    };
+    double prev64 = 0.0;
     long long prev = 0;
     for (int k = 0; k < c.K; ++k) {
-      const int32_t t = depth_fx(g, c.stp[k], c);
-      const double ref = rint(depth_f64(gd, c.stp64[k], c) * scale);
-      ldev = max(ldev, (int32_t)fmin(fabs((double)t - ref), 2.0e9));
+      const double t64 = depth_f64(gd, c.stp64[k], c) * scale;  // grid units
+      long long t;
+      if constexpr (kF64) {
+        t = clamp32(t64);
+        if (k > 0 && !(t64 > prev64) && bad == ~0ull && monotone)
+          bad = ((unsigned long long)i << 32) | (unsigned)k;
+      } else {
+        t = depth_fx(c.grp[i], c.stp[k], c);
+        ldev = max(ldev, clamp32(fabs((double)t - rint(t64))));
+      }
+      tlo = min(tlo, (int32_t)t);
+      thi = max(thi, (int32_t)t);
       if (k > 0) {
-        const long long st = (long long)t - prev;
+        const long long st = kF64 ? (long long)clamp32(t64 - prev64) : t - prev;
         lmin = (int32_t)min((long long)lmin, max(st, -2000000000ll));
         lmax = (int32_t)max((long long)lmax, min(st, 2000000000ll));
-        if ((st < kMinStepUnits || st >= kMaxStepUnits) && bad == ~0ull)
+        if (!kF64 && monotone && (st < kMinStepUnits || st >= kMaxStepUnits) && bad == ~0ull)
           bad = ((unsigned long long)i << 32) | (unsigned)k;
       }
       prev = t;
+      prev64 = t64;
     }
   }
   for (int m = 16; m > 0; m >>= 1) {
     lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, m));
     lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, m));
     ldev = max(ldev, __shfl_xor_sync(0xffffffffu, ldev, m));
+    tlo = min(tlo, __shfl_xor_sync(0xffffffffu, tlo, m));
+    thi = max(thi, __shfl_xor_sync(0xffffffffu, thi, m));
     const unsigned long long o = __shfl_xor_sync(0xffffffffu, bad, m);
     bad = o < bad ? o : bad;
   }
@@ -80,8 +101,93 @@ __global__ void __launch_bounds__(256) check_kernel(const Consts c, int ngroups,
     atomicMin(&res->min_step, lmin);
     atomicMax(&res->max_step, lmax);
     atomicMax(&res->max_dev, ldev);
+    atomicMin(&res->tmin, tlo);
+    atomicMax(&res->tmax, thi);
     if (bad != ~0ull) atomicMin(&res->bad, bad);
   }
+}
+
+// FP64 solution of the tangent condition (the plan's host solve_t, on the
+// device): t = z + Q0 + (a + sR dL(t)) / (D - eta), three fixed-point passes.
+__device__ double solve_t_dev(double Y, double Z, double y0, double sR, double D, double L0,
+                              double Q0, double z, double eta) {
+  const double Dm = D - eta;
+  const double a = y0 * z + eta * (z - Z + Q0);
+  double t = z + Q0 + a / Dm;
+  for (int it = 0; it < 3; ++it) {
+    const double u = Z - t;
+    const double L = sqrt(Y * Y + u * u);
+    const double dL = t * (t - 2.0 * Z) / (L + L0);
+    t = z + Q0 + (a + sR * dL) / Dm;
+  }
+  return t;
+}
+
+// Per-group constants of a plan, in FP64, from the affine pixel coordinates
+// Y = Y00 + r Yr + c Yc, Z = Z00 + r Zr + c Zc (group i is row i, or pixel
+// (i / W, i % W)): the FP64 mirror (GroupD) and the FP32 constants of the
+// plan's form of the remainder (GroupC; GroupPoly for the polynomial form:
+// the cubic through the remainder at four Chebyshev nodes of [zc - zh,
+// zc + zh], in grid units).
+__global__ void __launch_bounds__(256) groups_kernel(const GroupsParams q, GroupC *gc,
+                                                    GroupD *gd) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= q.ngroups) return;
+  const double r = q.rows_shared ? (double)i : (double)(i / q.W);
+  const double cc = q.rows_shared ? 0.0 : (double)(i % q.W);
+  const double Y = q.Y00 + r * q.Yr + cc * q.Yc, Z = q.Z00 + r * q.Zr + cc * q.Zc;
+  const double D = Y - q.y0, L0 = sqrt(Y * Y + Z * Z), Q0 = (-q.y0 * Z + q.sR * L0) / D;
+  gd[i] = GroupD{Z, Y * Y, L0, D, Q0};
+  const long long q0 = __double2ll_rn(Q0 * q.scale);
+  GroupC g;
+  if (q.mode == kDepthPoly) {
+    const double node[4] = {0.92387953251128674, 0.38268343236508978, -0.38268343236508978,
+                            -0.92387953251128674};
+    double x[4], v[4];
+    for (int n = 0; n < 4; ++n) {
+      x[n] = q.zh * node[n];
+      const double z = q.zc + x[n];
+      v[n] = (solve_t_dev(Y, Z, q.y0, q.sR, D, L0, Q0, z, 0.0) - z - Q0) * q.scale;
+    }
+    // Newton divided differences, then the monomial coefficients in d = z - zc
+    const double a0 = v[0];
+    const double d01 = (v[1] - v[0]) / (x[1] - x[0]), d12 = (v[2] - v[1]) / (x[2] - x[1]),
+                 d23 = (v[3] - v[2]) / (x[3] - x[2]);
+    const double d012 = (d12 - d01) / (x[2] - x[0]), d123 = (d23 - d12) / (x[3] - x[1]);
+    const double a1 = d01, a2 = d012, a3 = (d123 - d012) / (x[3] - x[0]);
+    GroupPoly p;
+    p.c3 = (float)a3;
+    p.c2 = (float)(a2 - a3 * (x[0] + x[1] + x[2]));
+    p.c1 = (float)(a1 - a2 * (x[0] + x[1]) + a3 * (x[0] * x[1] + x[0] * x[2] + x[1] * x[2]));
+    p.c0 = (float)(a0 - a1 * x[0] + a2 * x[0] * x[1] - a3 * x[0] * x[1] * x[2]);
+    p.unused0 = p.unused1 = p.unused2 = 0.f;
+    p.q0fx = (int32_t)(q0 - kRoundMagicBits);
+    memcpy(&g, &p, sizeof(g));
+  } else {
+    g.Z = (float)Z;
+    g.Y2 = (float)(Y * Y);
+    g.L0 = (float)L0;
+    g.invD = (float)(1.0 / D);
+    g.D = (float)D;
+    g.Q0f = (float)Q0;
+    g.Q0fx = (int32_t)q0;
+    g.invL0 = (float)(1.0 / L0);
+  }
+  gc[i] = g;
+}
+
+dr_status run_groups(const GroupsParams &q, GroupC *gc, GroupD *gd) {
+  if (q.ngroups <= 0) return DR_OK;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail("plan groups: stream", e);
+  groups_kernel<<<(unsigned)((q.ngroups + 255) / 256), 256, 0, st>>>(q, gc, gd);
+  e = cudaGetLastError();
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail("plan groups", e);
+  return DR_OK;
 }
 
 // Exact differences I_k - I_{k+1} as the kernels form them (int32 out).
@@ -146,10 +252,14 @@ template <class Geo, class OutT, bool kTma>
 dr_status launch_pixels(const dr_plan_t *p, const CUtensorMap &tm, const uint16_t *img,
                         void *out, cudaStream_t st) {
   // FP32 geometry: the walk takes at most one step per bin when the plan's
-  // check found every step at least as long as every bin
+  // check found every step at least as long as every bin; the polynomial
+  // form computes positions in the walk (pixels_poly_kernel)
   auto fn = pixels_kernel<Geo, OutT, kTma, false>;
   if constexpr (std::is_same<Geo, GeoFx>::value) {
-    if (p->one_adv) fn = pixels_kernel<Geo, OutT, kTma, true>;
+    if (p->c.depth_mode == kDepthPoly)
+      fn = p->one_adv ? pixels_poly_kernel<OutT, kTma, true> : pixels_poly_kernel<OutT, kTma, false>;
+    else if (p->one_adv)
+      fn = pixels_kernel<Geo, OutT, kTma, true>;
   }
   dr_status s = allow_smem((const void *)fn);
   if (s != DR_OK) return s;
@@ -189,17 +299,22 @@ dr_status dispatch_out(const dr_plan_t *p, bool tma, const CUtensorMap &tm, cons
 
 }  // namespace
 
-dr_status run_plan_check(const dr_plan_t *p, int ngroups, PlanCheck *d_res, PlanCheck *h_res) {
+dr_status run_plan_check(const dr_plan_t *p, int ngroups, bool monotone, PlanCheck *d_res,
+                         PlanCheck *h_res) {
   PlanCheck init;
   std::memset(&init, 0, sizeof(init));
   init.bad = ~0ull;
-  init.min_step = 0x7fffffff;
+  init.min_step = init.tmin = 0x7fffffff;
+  init.max_step = init.tmax = (int32_t)0x80000000;
   cudaStream_t st = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail("plan check: stream", e);
   e = cudaMemcpyAsync(d_res, &init, sizeof(init), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && ngroups > 0) {
-    check_kernel<<<(ngroups + 255) / 256, 256, 0, st>>>(p->c, ngroups, d_res);
+    if (p->geom_prec == DR_GEOM_FP64)
+      check_kernel<true><<<(ngroups + 255) / 256, 256, 0, st>>>(p->c, ngroups, monotone, d_res);
+    else
+      check_kernel<false><<<(ngroups + 255) / 256, 256, 0, st>>>(p->c, ngroups, monotone, d_res);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_res, d_res, sizeof(*h_res), cudaMemcpyDeviceToHost, st);
@@ -249,7 +364,17 @@ dr_status preload_kernels() {
       (const void *)pixels_kernel<GeoFx, float, false, false>,
       (const void *)pixels_kernel<GeoFx, __nv_bfloat16, true, false>,
       (const void *)pixels_kernel<GeoFx, __nv_bfloat16, false, false>,
-      (const void *)check_kernel,
+      (const void *)pixels_poly_kernel<float, true, true>,
+      (const void *)pixels_poly_kernel<float, false, true>,
+      (const void *)pixels_poly_kernel<__nv_bfloat16, true, true>,
+      (const void *)pixels_poly_kernel<__nv_bfloat16, false, true>,
+      (const void *)pixels_poly_kernel<float, true, false>,
+      (const void *)pixels_poly_kernel<float, false, false>,
+      (const void *)pixels_poly_kernel<__nv_bfloat16, true, false>,
+      (const void *)pixels_poly_kernel<__nv_bfloat16, false, false>,
+      (const void *)check_kernel<false>,
+      (const void *)check_kernel<true>,
+      (const void *)groups_kernel,
       (const void *)intervals_kernel<GeoFx, float, true>,
       (const void *)intervals_kernel<GeoFx, float, false>,
       (const void *)intervals_kernel<GeoFx, __nv_bfloat16, true>,

@@ -5,13 +5,16 @@
 // transfers over PCI Express as the bottleneck to hide by overlapping them
 // with computation; this runtime does that for a stream of requests.)
 //
-// One scheduler thread owns admission.  A request is admitted when a slot is
-// free and its image and output blocks fit in the arena (one cudaMalloc of the
-// budget made at creation, sub-allocated first-fit); plans are cached by their
-// geometry, wire path and bins.  Per request, on the slot's stream: upload,
-// host callback (upload time), dr_reconstruct, host callback (done time).  The
-// image block returns to the arena as soon as the kernel is done; the output
-// block when the client releases the request.
+// Planner threads build the plans of submitted requests while earlier
+// requests upload and run (plans are cached by their geometry, wire path and
+// bins; a queued request holds its plan).  One scheduler thread owns
+// admission: in arrival order, a request is admitted when its plan is ready,
+// a slot is free and its image and output blocks fit in the arena (one
+// cudaMalloc of the budget made at creation, sub-allocated first-fit).  Per
+// request, on the slot's stream: upload, host callback (upload time),
+// dr_reconstruct, host callback (done time).  The image block returns to the
+// arena as soon as the kernel is done; the output block when the client
+// releases the request.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,6 +35,8 @@
 using namespace dr;
 
 namespace {
+
+constexpr int kPlanners = 3;  // planner threads per server
 
 double now_s() {
   using namespace std::chrono;
@@ -88,9 +93,15 @@ class Arena {
   size_t size_ = 0, used_ = 0;
 };
 
+enum { kPlanBuilding = 0, kPlanReady = 1, kPlanFailed = 2 };
+
 struct PlanEntry {
   dr_plan_t *plan = nullptr;
-  int refs = 0;
+  int refs = 0;                // requests holding it (queued to released)
+  int state = kPlanBuilding;
+  dr_status status = DR_OK;    // of a failed build
+  double ready = 0;            // seconds since server creation
+  bool in_lru = false;
   std::list<std::string>::iterator lru;
 };
 
@@ -127,7 +138,10 @@ struct dr_server {
   std::vector<Request *> finished;     // kernels done, blocks not yet returned
   std::unordered_map<uint64_t, Request *> reqs;
   std::unordered_map<std::string, PlanEntry> plans;
-  std::list<std::string> lru;
+  std::list<std::string> lru;          // ready or failed plans, oldest use first
+  std::deque<Request *> plan_jobs;     // first request of each plan to build
+  std::condition_variable cv_plan;
+  std::vector<std::thread> planners;
   std::thread sched;
   bool stop = false;
   uint64_t next_id = 1;
@@ -181,16 +195,16 @@ void CUDART_CB on_done(void *arg) {
   s->cv_done.notify_all();
 }
 
-// Plans that no request uses, beyond the cache size, least recently used
+// Plans that no request holds, beyond the cache size, least recently used
 // first: taken out of the cache under the lock, destroyed by the caller after
-// unlocking (cudaFree synchronizes the device).
+// unlocking (no CUDA call under the lock).
 void evict_plans(dr_server_t *s, std::vector<dr_plan_t *> *dead) {
   while ((int)s->plans.size() > std::max(1, s->opt.plan_cache)) {
     bool evicted = false;
     for (auto l = s->lru.begin(); l != s->lru.end(); ++l) {
       auto pe = s->plans.find(*l);
       if (pe != s->plans.end() && pe->second.refs == 0) {
-        dead->push_back(pe->second.plan);
+        if (pe->second.plan) dead->push_back(pe->second.plan);
         s->plans.erase(pe);
         s->lru.erase(l);
         evicted = true;
@@ -198,6 +212,42 @@ void evict_plans(dr_server_t *s, std::vector<dr_plan_t *> *dead) {
       }
     }
     if (!evicted) break;
+  }
+}
+
+// A planner thread: builds the plan of the first request of each new key
+// (the request outlives the build: it cannot finish before its plan is
+// ready), without the lock while dr_plan runs.
+void planner(dr_server_t *s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    while (!s->stop && s->plan_jobs.empty()) s->cv_plan.wait(lk);
+    if (s->stop) return;
+    Request *r = s->plan_jobs.front();
+    s->plan_jobs.pop_front();
+    PlanEntry *pe = r->pe;
+    const dr_geometry g = r->g;
+    const std::vector<double> wires = r->wires, edges = r->edges;
+    const int K = r->K, B = r->B;
+    const std::string key = r->key;
+    lk.unlock();
+    dr_plan_t *p = nullptr;
+    dr_status st;
+    {
+      TraceRange trace_("server: plan of one request");
+      st = dr_plan(&g, wires.data(), K, edges.data(), B, nullptr, &p);
+    }
+    lk.lock();
+    pe->plan = p;
+    pe->state = st == DR_OK ? kPlanReady : kPlanFailed;
+    pe->status = st;
+    pe->ready = now_s() - s->t0;
+    if (st == DR_OK) s->plan_builds++;
+    s->lru.push_back(key);
+    pe->lru = std::prev(s->lru.end());
+    pe->in_lru = true;
+    s->cv_sched.notify_all();
   }
 }
 
@@ -227,10 +277,21 @@ void scheduler(dr_server_t *s) {
     }
     s->finished.clear();
     if (progress) s->cv_done.notify_all();
-    // choose admissions in arrival order while a slot and memory are free
+    // choose admissions in arrival order while the head's plan is ready and
+    // a slot and memory are free
     std::vector<Request *> admit;
     while (!s->queue.empty()) {
       Request *r = s->queue.front();
+      if (r->pe->state == kPlanBuilding) break;
+      if (r->pe->state == kPlanFailed) {
+        s->queue.pop_front();
+        const dr_status st = r->pe->status;
+        r->pe->refs--;
+        r->pe = nullptr;
+        fail(s, r, st);
+        progress = true;
+        continue;
+      }
       int slot = -1;
       for (int i = 0; i < (int)s->slot_busy.size(); ++i)
         if (!s->slot_busy[i]) {
@@ -258,50 +319,22 @@ void scheduler(dr_server_t *s) {
       s->slot_busy[slot] = 1;
       r->state = DR_REQ_UPLOADING;
       r->t.admitted = now_s() - s->t0;
+      r->t.planned = std::max(r->t.submitted, r->pe->ready);
       s->admitted++;
-      auto it = s->plans.find(r->key);
-      if (it != s->plans.end()) {
-        s->lru.splice(s->lru.end(), s->lru, it->second.lru);
-        it->second.refs++;
-        r->pe = &it->second;
-      }
+      if (r->pe->in_lru) s->lru.splice(s->lru.end(), s->lru, r->pe->lru);
       admit.push_back(r);
     }
-    if (admit.empty()) {
+    std::vector<dr_plan_t *> dead;
+    evict_plans(s, &dead);
+    if (admit.empty() && dead.empty()) {
       if (!progress) s->cv_sched.wait(lk);
       continue;
     }
     lk.unlock();  // ---- CUDA calls below, without the lock ----
     std::vector<std::pair<Request *, dr_status>> failed;
-    std::vector<dr_plan_t *> dead;
     for (Request *r : admit) {
-      TraceRange trace_("server: plan, upload and launch of one request");
+      TraceRange trace_("server: upload and launch of one request");
       dr_status st = DR_OK;
-      if (!r->pe) {
-        dr_plan_t *p = nullptr;
-        st = dr_plan(&r->g, r->wires.data(), r->K, r->edges.data(), r->B, nullptr, &p);
-        if (st == DR_OK) {
-          std::lock_guard<std::mutex> g(s->mu);
-          s->plan_builds++;
-          auto it = s->plans.find(r->key);
-          if (it == s->plans.end()) {
-            s->lru.push_back(r->key);
-            PlanEntry e;
-            e.plan = p;
-            e.lru = std::prev(s->lru.end());
-            it = s->plans.emplace(r->key, e).first;
-          } else {
-            dead.push_back(p);  // an earlier admission of this batch built it
-          }
-          it->second.refs++;
-          r->pe = &it->second;
-          evict_plans(s, &dead);
-        }
-      }
-      {
-        std::lock_guard<std::mutex> g(s->mu);
-        r->t.planned = now_s() - s->t0;
-      }
       cudaStream_t cs = s->streams[r->slot];
       uint16_t *d_img = reinterpret_cast<uint16_t *>(s->base + r->img_off);
       void *d_out = s->base + r->out_off;
@@ -399,6 +432,7 @@ extern "C" dr_status dr_server_create(const dr_server_options *o, dr_server_t **
   }
   s->t0 = now_s();
   s->sched = std::thread(scheduler, s);
+  for (int i = 0; i < kPlanners; ++i) s->planners.emplace_back(planner, s);
   *out = s;
   return DR_OK;
 }
@@ -436,9 +470,18 @@ extern "C" dr_status dr_server_submit(dr_server_t *s, const dr_geometry *g, cons
     r->id = s->next_id++;
     r->t.submitted = now_s() - s->t0;
     s->reqs[r->id] = r;
+    auto it = s->plans.find(r->key);
+    if (it == s->plans.end()) {  // a new plan: to the planners
+      it = s->plans.emplace(r->key, PlanEntry()).first;
+      r->pe = &it->second;
+      s->plan_jobs.push_back(r);
+    }
+    it->second.refs++;
+    r->pe = &it->second;
     s->queue.push_back(r);
     *id = r->id;
   }
+  s->cv_plan.notify_one();
   s->cv_sched.notify_all();
   return DR_OK;
 }
@@ -587,7 +630,10 @@ extern "C" void dr_server_destroy(dr_server_t *s) {
     s->stop = true;
   }
   s->cv_sched.notify_all();
+  s->cv_plan.notify_all();
   if (s->sched.joinable()) s->sched.join();
+  for (auto &t : s->planners)
+    if (t.joinable()) t.join();
   if (s->up) {
     cudaStreamSynchronize(s->up);
     cudaStreamDestroy(s->up);
@@ -600,7 +646,8 @@ extern "C" void dr_server_destroy(dr_server_t *s) {
   for (auto ev : s->up_done)
     if (ev) cudaEventDestroy(ev);
   for (auto &kv : s->reqs) delete kv.second;
-  for (auto &kv : s->plans) dr_plan_destroy(kv.second.plan);
+  for (auto &kv : s->plans)
+    if (kv.second.plan) dr_plan_destroy(kv.second.plan);
   if (s->base) cudaFree(s->base);
   delete s;
 }

@@ -24,13 +24,19 @@
 // positions are exact.  dL enters scaled by R / D ~ 5e-5, so evaluating it
 // at the estimate without the dL term leaves an error ~1e-10 mm.
 //
-// dL itself has two forms.  The exact one takes a square root and a
-// reciprocal: dL = t (t - 2Z) / (L(t) + L0).  With n = t (t - 2Z) =
-// L(t)^2 - L0^2 and x = n / L0^2 it is also L0 (sqrt(1 + x) - 1) =
-// n / (2 L0) (1 - x/4 + x^2/8 - 5x^3/64 + ...); the series form keeps three
-// terms (only multiply-adds).  A plan uses the series where the first dropped
-// term stays far below one grid unit, and its check compares every depth the
-// kernels compute with the FP64 solution.
+// The remainder is computed in one of three forms (Consts::depth_mode):
+//  * exact: dL = t (t - 2Z) / (L(t) + L0), a square root and a reciprocal;
+//  * series: with n = t (t - 2Z) = L(t)^2 - L0^2 and x = n / L0^2,
+//    dL = L0 (sqrt(1 + x) - 1) = n / (2 L0) (1 - x/4 + x^2/8 - 5x^3/64 + ...),
+//    three terms (multiply-adds only);
+//  * polynomial: when every wire centre has the same distance from the beam
+//    (eta = 0) the remainder of a group is a smooth function of z_k alone;
+//    the plan interpolates it in FP64 by a cubic in (z_k - z_c) through four
+//    Chebyshev nodes of the path's z range, in grid units, so a position is
+//    three multiply-adds and a rounding.
+// A plan takes the cheapest form whose error it can bound far below one grid
+// unit, and its check compares every depth the kernels compute with the FP64
+// solution (falling back to the next form if the bound does not hold).
 #pragma once
 
 #include <cstddef>
@@ -48,12 +54,26 @@ struct GroupC {
 };
 static_assert(sizeof(GroupC) == 32, "GroupC layout");
 
+// The same 32 bytes in the polynomial form: the remainder of the group in
+// grid units is ((c3 d + c2) d + c1) d + c0 with d = z_k - z_c (StepC::dz),
+// and q0fx = round(Q0 * 2^shift) - 0x4B400000 (the bias of the rounding by
+// 1.5 * 2^23 folded in).
+struct GroupPoly {
+  float c0, c1, c2, c3;
+  float unused0, unused1;
+  int32_t q0fx;
+  float unused2;
+};
+static_assert(sizeof(GroupPoly) == sizeof(GroupC), "GroupPoly layout");
+
 struct StepC {
   float zf, eta;           // z_k, eta_k (FP32)
   int32_t zfx;             // round((z_k - origin) * 2^shift)
-  float pad;
+  float dz;                // z_k - z_c (polynomial form)
 };
 static_assert(sizeof(StepC) == 16, "StepC layout");
+
+enum : int { kDepthExact = 0, kDepthSeries = 1, kDepthPoly = 2 };
 
 // FP64 mirrors for the all-FP64 geometry variant.
 struct GroupD {
@@ -88,8 +108,8 @@ struct Consts {
   // 1: add this plan's bins to the output instead of writing them (the later
   // parts of a composite plan: monotone runs, both wire edges)
   int accumulate;
-  // 1: FP32 geometry evaluates dL by its series (see above), 0: exact form
-  int depth_series;
+  // form of the FP32 remainder (kDepthExact / kDepthSeries / kDepthPoly)
+  int depth_mode;
 };
 
 // What the plan-time check of every (group, step) found (device, written by
@@ -101,6 +121,7 @@ struct PlanCheck {
   unsigned long long bad;  // (group << 32) | step of the first failure; ~0 if none
   int32_t min_step, max_step;
   int32_t max_dev;         // max |t_fp32 - round(t_fp64 * 2^shift)|
+  int32_t tmin, tmax;      // range of all positions
   int32_t pad;
 };
 // Steps of FP32 positions must span at least this many grid units (a few

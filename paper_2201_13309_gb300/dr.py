@@ -23,6 +23,7 @@ STATUS = {0: "DR_OK", 1: "DR_ERR_INVALID_ARG", 2: "DR_ERR_GEOMETRY",
 EDGES = {"leading": 0, "trailing": 1, "both": 2}
 OUT_DTYPES = {"f32": 0, "bf16": 1}
 GEOM_PRECISIONS = {"fp32": 0, "fp64": 1}
+DEPTH_FORMS = {"auto": 0, "exact": 1, "series": 2, "poly": 3}
 KERNELS = {0: "rows", 1: "pixels", 2: "intervals"}
 
 # every symbol include/dr.h declares (checked by the CPU tests)
@@ -53,7 +54,7 @@ class PlanOptions(ctypes.Structure):
     _fields_ = [("out_dtype", ctypes.c_int32), ("geom_precision", ctypes.c_int32),
                 ("tile_cols", ctypes.c_int32), ("bin_groups", ctypes.c_int32),
                 ("force_pixels", ctypes.c_int32), ("force_intervals", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("depth_form", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -64,7 +65,7 @@ class PlanInfo(ctypes.Structure):
         ("depth_min", ctypes.c_double), ("depth_max", ctypes.c_double),
         ("min_step", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
         ("bytes_per_call", ctypes.c_double), ("max_step", ctypes.c_double),
-        ("depth_err", ctypes.c_double), ("depth_series", ctypes.c_int32),
+        ("depth_err", ctypes.c_double), ("depth_form", ctypes.c_int32),
         ("one_step_per_bin", ctypes.c_int32), ("checked_groups", ctypes.c_int64)]
 
     def as_dict(self):
@@ -214,12 +215,14 @@ class Plan:
     "both"; out_dtype "f32" / "bf16"; geom_precision "fp32" / "fp64";
     tile_cols / bin_groups: launch shape (0 = default); force_pixels /
     force_intervals: use the per-pixel or the interval kernel instead of the
-    one the plan picks (info()["kernel"] tells which).
+    one the plan picks (info()["kernel"] tells which); depth_form: "auto",
+    or the most elaborate form of the FP32 depth remainder the plan may use
+    ("exact", "series", "poly"; info()["depth_form"] tells which it took).
     """
 
     def __init__(self, geom, wires, edges, edge="leading", out_dtype="f32",
                  geom_precision="fp32", tile_cols=0, bin_groups=0, force_pixels=False,
-                 force_intervals=False):
+                 force_intervals=False, depth_form="auto"):
         L = lib()
         self._wires = np.ascontiguousarray(wires, dtype=np.float64)
         self._edges = np.ascontiguousarray(edges, dtype=np.float64)
@@ -234,6 +237,7 @@ class Plan:
         o.bin_groups = int(bin_groups)
         o.force_pixels = 1 if force_pixels else 0
         o.force_intervals = 1 if force_intervals else 0
+        o.depth_form = DEPTH_FORMS[depth_form]
         h = ctypes.c_void_p()
         check(L.dr_plan(ctypes.byref(g), self._wires.ctypes.data_as(ctypes.c_void_p),
                         self._wires.shape[0], self._edges.ctypes.data_as(ctypes.c_void_p),

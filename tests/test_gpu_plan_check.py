@@ -53,14 +53,15 @@ def test_plan_reports_every_pixels_steps(rotate, tilt):
                   .cpu().numpy(), ref_of(sc), sc.images)
 
 
-def test_series_form_on_the_beamline_geometry():
-    """The beamline scan takes the series form of dL; its depths stay within
-    the FP32 bar of the oracle, for the rows and the per-pixel plans."""
+def test_polynomial_form_on_the_beamline_geometry():
+    """The beamline scan takes the polynomial form of the remainder; its
+    depths stay within the FP32 bar of the oracle, for the rows and the
+    per-pixel plans."""
     sc = synth.tiny_scan(5)
     for kw in ({}, {"force_pixels": True}):
         plan = dr.Plan(sc.geom, sc.wires, sc.edges, **kw)
         info = plan.info()
-        assert info["depth_series"] == 1 and info["one_step_per_bin"] == 1
+        assert info["depth_form"] == 2 and info["one_step_per_bin"] == 1
         unit = 2.0 ** -info["fixed_shift"]
         err = np.abs(plan.depths().cpu().numpy() - O.depths(sc.geom, sc.wires)).max()
         assert err < 4 * unit and info["depth_err"] < 4 * unit
@@ -101,3 +102,38 @@ def test_step_sign_change_between_sampled_rows_takes_interval_kernel(band_row):
         plan, out = run(sc, **kw)
         assert plan.info()["kernel"] == "intervals"
         assert_parity(out.cpu().numpy(), ref_of(sc), sc.images)
+
+
+@pytest.mark.parametrize("form", ["exact", "series", "poly"])
+def test_each_depth_form_against_the_oracle(form):
+    """Every form of the FP32 remainder (exact, series of dL, per-pixel
+    cubic in the wire position), asked for explicitly: depths within the
+    FP32 bar of the oracle, the plan's own error figure consistent with
+    them, and the reconstruction within tolerance; rows and per-pixel plans."""
+    rot = synth.spot_scan(9, 20, 64, 41, 6, -60, 60, 1.0, roi_origin=(1000, 300),
+                          det_rows=2048, det_cols=2048, rotate_deg=12.0, tilt_deg=3.0,
+                          depth_range=(-0.03, 0.03))
+    row = synth.spot_scan(10, 30, 48, 45, 6, -60, 60, 1.0, roi_origin=(1800, 0),
+                          det_rows=2048, det_cols=2048, depth_range=(-0.03, 0.03))
+    want = {"exact": 0, "series": 1, "poly": 2}[form]
+    for sc, kernel in ((rot, "pixels"), (row, "rows")):
+        plan = dr.Plan(sc.geom, sc.wires, sc.edges, depth_form=form)
+        info = plan.info()
+        assert (info["kernel"], info["depth_form"]) == (kernel, want)
+        unit = 2.0 ** -info["fixed_shift"]
+        err = np.abs(plan.depths().cpu().numpy() - O.depths(sc.geom, sc.wires)).max()
+        assert err < 4 * unit and abs(err - info["depth_err"]) < 1.5 * unit + 1e-12
+        out = plan.reconstruct(torch.from_numpy(sc.images.view(np.int16)).cuda())
+        torch.cuda.synchronize()
+        assert_parity(out.cpu().numpy(), ref_of(sc), sc.images)
+
+
+def test_climbing_wire_takes_the_exact_form():
+    """A wire that also moves across the beam (eta != 0) has a remainder
+    that depends on more than the wire's position along the beam: the plan
+    keeps the exact form."""
+    sc = synth.tiny_scan(8, rows=6, cols=40, K=25, roi_origin=(1000, 600), det_rows=2048,
+                         det_cols=2048)
+    sc.wires = synth.wire_path(25, dy=0.0002)
+    plan = dr.Plan(sc.geom, sc.wires, sc.edges)
+    assert plan.info()["depth_form"] == 0
