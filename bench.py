@@ -582,6 +582,9 @@ def run_served(args, dev):
     results = []
     rates = [float(r) for r in args.rates.split(",") if r]
     srv = dr.Server(budget, slots=args.slots)
+    # per-request timestamps (seconds since the server's creation), one JSON
+    # object per line, when asked for
+    trace = open(args.served_trace, "w") if args.served_trace else None
     for ri, rate in enumerate(rates):
         specs = [synth.batch_scan_spec(100000 * (ri + 1) + i) for i in range(args.served_scans)]
         rng = np.random.Generator(np.random.PCG64(1000 + int(rate)))
@@ -600,9 +603,12 @@ def run_served(args, dev):
                 _, t = srv.fetch(rid)
                 lat.append(t["done"] - t["submitted"])
                 sp = specs[i]
-                parts.append((sp.P * sp.K * 2, t["admitted"] - t["submitted"],
-                              t["planned"] - t["admitted"], t["uploaded"] - t["planned"],
+                parts.append((sp.P * sp.K * 2, t["planned"] - t["submitted"],
+                              t["admitted"] - t["submitted"], t["uploaded"] - t["admitted"],
                               t["done"] - t["uploaded"]))
+                if trace is not None:
+                    trace.write(json.dumps(dict(t, rate=rate, i=i, rows=sp.geom["rows"],
+                                                cols=sp.geom["cols"], K=sp.K, B=sp.B)) + "\n")
                 srv.release(rid)
 
         ct = th.Thread(target=consumer)
@@ -625,7 +631,9 @@ def run_served(args, dev):
         pa = np.array([p[1:] for p in parts]) * 1e3
         in_gb = np.array([p[0] for p in parts]) / 1e9
         big = in_gb >= np.percentile(in_gb, 90)
-        names = ("queue", "plan", "upload", "kernel")
+        # phases from arrival: plan ready, admitted (plan ready, slot and
+        # memory free), upload done (after earlier uploads), kernel done
+        names = ("plan_wait", "queue", "upload", "kernel")
         results.append({"offered_scans_per_s": rate, "scans": args.served_scans,
                         "achieved_scans_per_s": args.served_scans / wall,
                         "plans_built": srv.stats()["plans_built"] - built0,
@@ -643,6 +651,8 @@ def run_served(args, dev):
                             "upload_GBps_p50": float(np.percentile(
                                 in_gb[big] / np.maximum(pa[big, 2] * 1e-3, 1e-9), 50))}})
         print(json.dumps({"served_rate": results[-1]}), file=sys.stderr, flush=True)
+    if trace is not None:
+        trace.close()
     st = srv.stats()
     srv.close()
     # saturation: everything submitted at once, against the serial loop over
@@ -749,6 +759,8 @@ def main():
     ap.add_argument("--rates", default="5,20,50")
     ap.add_argument("--served-scans", type=int, default=1000)
     ap.add_argument("--saturation-scans", type=int, default=96)
+    ap.add_argument("--served-trace", default="",
+                    help="served: write every request's timestamps to this file")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--batch-scans", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)

@@ -247,7 +247,10 @@ dr_status dr_plan_depths(const dr_plan_t *plan, int32_t r0, int32_t nrows,
                          double *d_depths, dr_stream_t stream);
 
 /* Read and clear the plan's device error word (set by a kernel whose bounded
- * wait ran out).  Synchronizes the device.  DR_OK or DR_ERR_TIMEOUT. */
+ * wait ran out).  Synchronizes the device.  DR_OK or DR_ERR_TIMEOUT; in the
+ * bounds-checked test build of the library (compiled with DR_CHECK_BOUNDS)
+ * also DR_ERR_CUDA when a kernel index was out of range (dr_last_error names
+ * the device-source line). */
 dr_status dr_plan_check(const dr_plan_t *plan);
 
 /* Failure-path diagnostic (no counterpart in the paper): launches one CTA on
@@ -322,11 +325,13 @@ dr_status dr_batch_reconstruct(const dr_job *jobs, int32_t n, const dr_batch_opt
  * host<->device transfers as the cost to hide by overlapping them with
  * computation; here each request's pinned-host upload overlaps other
  * requests' kernels).  At creation the server reserves budget_bytes of device
- * memory (one cudaMalloc) and starts a scheduler thread.  Requests are admitted
- * in arrival order as soon as a slot (a stream) is free and their image and
- * output blocks fit in the reserved memory; a request larger than the whole
- * budget fails with DR_ERR_BUDGET.  Plans are cached by geometry, wire path
- * and bins.  A request's image block is returned when its kernel finishes;
+ * memory (one cudaMalloc) and starts a scheduler thread and planner threads.
+ * Plans are cached by geometry, wire path and bins; a submitted request whose
+ * plan is not cached has it built by a planner thread while earlier requests
+ * upload and run.  Requests are admitted in arrival order as soon as their
+ * plan is ready, a slot (a stream) is free and their image and output blocks
+ * fit in the reserved memory; a request larger than the whole budget fails
+ * with DR_ERR_BUDGET.  A request's image block is returned when its kernel finishes;
  * its output stays on the device until dr_server_release.  Results are
  * bitwise identical to dr_reconstruct's, alone or in any mix. */
 typedef struct dr_server dr_server_t;
@@ -341,9 +346,11 @@ typedef struct {
 enum { DR_REQ_QUEUED = 0, DR_REQ_UPLOADING = 1, DR_REQ_RUNNING = 2, DR_REQ_DONE = 3,
        DR_REQ_FAILED = 4 };
 
-/* Seconds since the server was created (host steady clock): queued, admitted
- * (slot and memory reserved), planned (plan found or built), uploaded (the
- * upload, which waits behind earlier uploads, is done), done (kernel done). */
+/* Seconds since the server was created (host steady clock): submitted,
+ * planned (the request's plan was ready: found in the cache at submission,
+ * or built by a planner thread while the request waited), admitted (plan
+ * ready, slot and memory reserved), uploaded (the upload, which waits behind
+ * earlier uploads, is done), done (kernel done). */
 typedef struct {
   double submitted, admitted, planned, uploaded, done;
 } dr_request_times;

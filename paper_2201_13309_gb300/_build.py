@@ -18,6 +18,10 @@ import tempfile
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libdr.so")
+# the bounds-checked build (DR_CHECK_BOUNDS: every kernel index checked, an
+# out-of-range one recorded in the plan's error word): a test build, never
+# loaded by default
+LIB_CHECKED = os.path.join(HERE, "libdr_checked.so")
 SOURCES = ["dr_plan.cu", "dr_recon.cu", "dr_batch.cu", "dr_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -31,20 +35,22 @@ def nvcc():
     return path
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def _stale(lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "dr.h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, ptxas_info=False):
-    """Build libdr.so if any source is newer than it; returns its path."""
-    if not force and not _stale():
-        return LIB
+def build(force=False, verbose=False, ptxas_info=False, checked=False):
+    """Build libdr.so (checked=True: libdr_checked.so with DR_CHECK_BOUNDS)
+    if any source is newer than it; returns its path."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not _stale(lib):
+        return lib
     cc = nvcc()
     tmp = tempfile.mkdtemp(prefix="drbuild")
     try:
@@ -53,6 +59,8 @@ def build(force=False, verbose=False, ptxas_info=False):
             obj = os.path.join(tmp, src.replace(".cu", ".o"))
             cmd = [cc, *ARCH, *FLAGS, "-I", os.path.join(os.path.dirname(HERE), "include"),
                    "-c", os.path.join(CSRC, src), "-o", obj]
+            if checked:
+                cmd.append("-DDR_CHECK_BOUNDS")
             if ptxas_info:
                 cmd += ["-Xptxas", "-v"]
             if verbose:
@@ -69,14 +77,14 @@ def build(force=False, verbose=False, ptxas_info=False):
                 print(out, file=sys.stderr)
         if failed:
             raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
-        tmp_lib = LIB + f".tmp{os.getpid()}"
+        tmp_lib = lib + f".tmp{os.getpid()}"
         cudalib = os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")
         subprocess.run([cc, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", "-rpath",
                         "-Xlinker", cudalib, "-o", tmp_lib, *objs], check=True)
-        os.replace(tmp_lib, LIB)
+        os.replace(tmp_lib, lib)
     finally:
         shutil.rmtree(tmp, ignore_errors=True)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -48,8 +48,8 @@ void destroy(dr_batch_t *b) {
 }
 
 template <class OutT>
-const void *batch_fn() {
-  return (const void *)batch_kernel<OutT>;
+const void *batch_fn(bool poly_only) {
+  return poly_only ? (const void *)batch_kernel<OutT, true> : (const void *)batch_kernel<OutT, false>;
 }
 
 }  // namespace
@@ -77,6 +77,7 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
   std::vector<BatchScan> desc(n);
   std::vector<double> cost(n);
   int smem_max = 0, out_dtype = -1;
+  bool poly_only = true;
   for (int i = 0; i < n; ++i) {
     const dr_plan_t *p = jobs[i].plan;
     if (!p) {
@@ -119,8 +120,10 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
       }
       lanes = t.tile_cols / 4;
     } else {
-      t.tile_cols = 32;
+      // the polynomial form's tile holds no depth table: 64 columns when
+      // they fit (the plain kernel's tuned width), else narrower
       const bool poly = p->c.depth_mode == kDepthPoly;
+      t.tile_cols = poly && nthreads >= 512 ? 64 : 32;
       for (;;) {
         choose_chunks(p->K, t.tile_cols, &t.kc, &t.nchunks);
         smem = poly ? pixels_poly_smem_bytes(p->K, t.kc * t.nchunks, p->B, t.tile_cols)
@@ -150,6 +153,7 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
       d.kind = p->one_adv ? kBatchPixelsPolyOneAdv : kBatchPixelsPoly;
     else
       d.kind = p->one_adv ? kBatchPixelsOneAdv : kBatchPixels;
+    poly_only &= d.kind == kBatchPixelsPolyOneAdv || d.kind == kBatchPixelsPoly;
     if (P > 0) {
       dr_plan_t tmp = *p;
       tmp.tune = t;
@@ -182,7 +186,8 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
   b->n_items = items;
   b->out_dtype = out_dtype;
   b->smem = smem_max;
-  const void *fn = out_dtype == DR_OUT_BF16 ? batch_fn<__nv_bfloat16>() : batch_fn<float>();
+  const void *fn = out_dtype == DR_OUT_BF16 ? batch_fn<__nv_bfloat16>(poly_only)
+                                            : batch_fn<float>(poly_only);
   dr_status s = allow_smem(fn);
   if (s != DR_OK) {
     destroy(b);
@@ -234,12 +239,8 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
     cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->cap);
     if (items > 0) {
       const int ns = (int)sorted.size();
-      if (out_dtype == DR_OUT_BF16)
-        batch_kernel<__nv_bfloat16><<<b->grid, nthreads, smem_max, b->cap>>>(
-            b->d_scans, ns, items, b->d_counter);
-      else
-        batch_kernel<float><<<b->grid, nthreads, smem_max, b->cap>>>(
-            b->d_scans, ns, items, b->d_counter);
+      void *args[] = {&b->d_scans, const_cast<int *>(&ns), &items, &b->d_counter};
+      e = cudaLaunchKernel(fn, dim3(b->grid), dim3(nthreads), args, smem_max, b->cap);
     }
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &b->graph);
     e = e2 != cudaSuccess ? e2 : cudaGetLastError();

@@ -86,6 +86,27 @@ __device__ inline bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int32_t
   return true;
 }
 
+// ------------------------------------------------------- checked build ---
+// Built with -DDR_CHECK_BOUNDS (off by default: the normal build compiles
+// every index unchanged), each shared-memory and global index of the
+// reconstruction kernels goes through DR_IDX: an index outside [0, n)
+// records kDevBounds with the source line in the error word (the first one
+// found stays) and is replaced by 0, so the access stays inside its array and
+// nothing traps.  DR_PTR does the same for a pointer walking an array.
+#ifdef DR_CHECK_BOUNDS
+#define DR_IDX(i, n, err) ::dr::checked_index((long long)(i), (long long)(n), (err), __LINE__)
+#define DR_PTR(p, base, n, err) ((base) + DR_IDX((p) - (base), (n), (err)))
+__device__ __forceinline__ long long checked_index(long long i, long long n, int32_t *err,
+                                                   int line) {
+  if (i >= 0 && i < n) return i;
+  atomicCAS(err, 0, kDevBounds | (line << 4));
+  return 0;
+}
+#else
+#define DR_IDX(i, n, err) (i)
+#define DR_PTR(p, base, n, err) (p)
+#endif
+
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -496,9 +517,12 @@ __device__ __forceinline__ void stage_tile(const CUtensorMap *tmap, const uint16
     }
   } else {
     const int n = c.K * TC;
+    const size_t n_img = (size_t)c.K * c.H * c.W;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int k = i / TC, cc = i - k * TC, col = c0 + cc;
-      simg[i] = col < c.W ? img[((size_t)k * c.H + row) * c.W + col] : (uint16_t)0;
+      simg[DR_IDX(i, (size_t)t.kc * t.nchunks * TC, c.err)] =
+          col < c.W ? img[DR_IDX(((size_t)k * c.H + row) * c.W + col, n_img, c.err)]
+                    : (uint16_t)0;
     }
   }
 }
@@ -523,7 +547,7 @@ __device__ __forceinline__ int2 build_row_table(const Consts &c, int row,
   const int K = c.K, B = c.B, tid = threadIdx.x, NT = blockDim.x;
   const auto &g = Geo::group(c, row);
   const auto *steps = Geo::steps(c);
-  for (int k = tid; k < K; k += NT) spos[k] = Geo::depth(g, steps[k], c);
+  for (int k = tid; k < K; k += NT) spos[DR_IDX(k, K, c.err)] = Geo::depth(g, steps[k], c);
   __syncthreads();
   int below = 0, above = 0;
   const pos_t tfirst = spos[0], tlast = spos[K - 1];
@@ -532,11 +556,12 @@ __device__ __forceinline__ int2 build_row_table(const Consts &c, int row,
     int lo = 0, hi = K;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (spos[mid] < e) lo = mid + 1; else hi = mid;
+      if (spos[DR_IDX(mid, K, c.err)] < e) lo = mid + 1; else hi = mid;
     }
     const int k = min(max(lo - 1, 0), K - 2);
-    const float f = Geo::frac(e, spos[k], spos[k + 1], Geo::inv_len(spos[k], spos[k + 1]));
-    out1[j] = make_int2(k, __float_as_int(f));
+    const pos_t a = spos[DR_IDX(k, K, c.err)], b = spos[DR_IDX(k + 1, K, c.err)];
+    const float f = Geo::frac(e, a, b, Geo::inv_len(a, b));
+    out1[DR_IDX(j, B + 1, c.err)] = make_int2(k, __float_as_int(f));
     below += !(e > tfirst);
     above += !(e < tlast);
   }
@@ -626,13 +651,15 @@ __device__ __forceinline__ bool rows_tile(const CUtensorMap *tmap, const uint16_
   const size_t plane = (size_t)c.H * c.W;
   OutT *const o0 = out + (size_t)row * c.W + col;
   const bool acc = c.accumulate != 0;
+  const size_t n_out = plane * B - (PPT - 1);  // first elements of in-range stores
   float zero[PPT];
 #pragma unroll
   for (int i = 0; i < PPT; ++i) zero[i] = __fmul_rn(sign, 0.f);
   auto zero_fill = [&](int a, int b) {
     OutT *o = o0 + (size_t)a * plane;
 #pragma unroll 4
-    for (int j = a; j < b; ++j, o += plane) store_px<OutT, PPT>(o, zero);
+    for (int j = a; j < b; ++j, o += plane)
+      store_px<OutT, PPT>(DR_PTR(o, out, n_out, c.err), zero);
   };
   if (!acc) {  // bins without data: written as zero (nothing to add when accumulating)
     zero_fill(slice_lo(0, nz_lo), slice_hi(0, nz_lo));
@@ -642,7 +669,10 @@ __device__ __forceinline__ bool rows_tile(const CUtensorMap *tmap, const uint16_
   const int a = slice_lo(nz_lo, nz_hi), b = slice_hi(nz_lo, nz_hi);
   if (a >= b) return true;
   const bool rev = c.reverse != 0;
-  auto srow = [&](int k) { return simg + (size_t)(rev ? K - 1 - k : k) * TC + lc; };
+  const size_t n_simg = (size_t)Kpad * TC - (PPT - 1);
+  auto srow = [&](int k) {
+    return simg + DR_IDX((size_t)(rev ? K - 1 - k : k) * TC + lc, n_simg, c.err);
+  };
   float I0[PPT];
   load_px<PPT>(srow(0), I0);
   auto evalF = [&](int2 kf, float (&F)[PPT]) {
@@ -658,12 +688,12 @@ __device__ __forceinline__ bool rows_tile(const CUtensorMap *tmap, const uint16_
   auto stream = [&](auto add) {
     constexpr bool kAdd = decltype(add)::value;
     float Fp[PPT];
-    evalF(stab[a], Fp);
+    evalF(stab[DR_IDX(a, B + 1, c.err)], Fp);
     OutT *o = o0 + (size_t)a * plane;
 #pragma unroll 4
     for (int j = a; j < b; ++j, o += plane) {
       float Fn[PPT], v[PPT];
-      evalF(stab[j + 1], Fn);
+      evalF(stab[DR_IDX(j + 1, B + 1, c.err)], Fn);
 #pragma unroll
       for (int i = 0; i < PPT; ++i) {
         v[i] = __fmul_rn(sign, __fsub_rn(Fn[i], Fp[i]));
@@ -671,11 +701,11 @@ __device__ __forceinline__ bool rows_tile(const CUtensorMap *tmap, const uint16_
       }
       if constexpr (kAdd) {
         float old[PPT];
-        load_out_px<OutT, PPT>(o, old);
+        load_out_px<OutT, PPT>(DR_PTR(o, out, n_out, c.err), old);
 #pragma unroll
         for (int i = 0; i < PPT; ++i) v[i] = __fadd_rn(old[i], v[i]);
       }
-      store_px<OutT, PPT>(o, v);
+      store_px<OutT, PPT>(DR_PTR(o, out, n_out, c.err), v);
     }
   };
   if (acc)
@@ -781,8 +811,8 @@ __device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint1
         const int k2 = min(k + G, K - 1);
         pos_t d0, d1;
         depth2(g, gsteps[k], gsteps[k2], c, d0, d1);
-        spos[k * TC + lc] = d0;
-        if (k + G < K) spos[(k + G) * TC + lc] = d1;
+        spos[DR_IDX(k * TC + lc, K * TC, c.err)] = d0;
+        if (k + G < K) spos[DR_IDX((k + G) * TC + lc, K * TC, c.err)] = d1;
       }
     };
     if constexpr (kFx) {
@@ -802,9 +832,9 @@ __device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint1
               pos_t &d1) { Geo::depth2(g, s0, s1, c, d0, d1); });
     }
   }
-  for (int j = tid; j <= B; j += NT) sedge[j] = Geo::edge(c, j);
+  for (int j = tid; j <= B; j += NT) sedge[DR_IDX(j, B + 1, c.err)] = Geo::edge(c, j);
   __syncthreads();  // also makes the mbarrier initialisation visible
-  auto pos = [&](int k) { return spos[k * TC + lc]; };
+  auto pos = [&](int k) { return spos[DR_IDX(k * TC + lc, K * TC, c.err)]; };
   // Counts on the sorted edges and depths, guessed by linear interpolation
   // (uniform bins, near-uniform depth steps), checked against the two
   // neighbours and moved by up to two places; a binary search otherwise.
@@ -833,9 +863,9 @@ __device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint1
   const pos_t lo_d = group_min(valid ? pos(0) : sedge[B], SW);
   const pos_t hi_d = group_max(valid ? pos(K - 1) : sedge[0], SW);
   const int n_le = count_prefix(((float)lo_d - (float)e0) * bins_per_pos + 1.f, B + 1,
-                                [&](int i) { return !(sedge[i] > lo_d); });
+                                [&](int i) { return !(sedge[DR_IDX(i, B + 1, c.err)] > lo_d); });
   const int n_lt = count_prefix(((float)hi_d - (float)e0) * bins_per_pos + 1.f, B + 1,
-                                [&](int i) { return sedge[i] < hi_d; });
+                                [&](int i) { return sedge[DR_IDX(i, B + 1, c.err)] < hi_d; });
   const int jlo = min(max(n_le - 1, 0), B);
   const int2 sp = make_int2(jlo, max(min(n_lt, B), jlo));
   if constexpr (kTma) {
@@ -858,12 +888,13 @@ __device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint1
       for (int i = share * SW + sl; i < nz * kVec; i += G * SW) {
         const int z = i >> kvl, part = i & (kVec - 1);
         const int j = z < sp.x ? z : z - sp.x + sp.y;
-        st_cs_u4(os + (size_t)j * plane + part * kPer, zv);
+        st_cs_u4(DR_PTR(os + (size_t)j * plane + part * kPer, out, plane * B - (kPer - 1), c.err),
+                 zv);
       }
     } else if (valid) {
       for (int z = share; z < nz; z += G) {
         const int j = z < sp.x ? z : z - sp.x + sp.y;
-        st_cs(os + (size_t)j * plane + sl, zero);
+        st_cs(DR_PTR(os + (size_t)j * plane + sl, out, plane * B, c.err), zero);
       }
     }
   }
@@ -880,12 +911,12 @@ __device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint1
   const uint16_t *ip = simg + (rev ? (K - 1) * TC : 0) + lc;
   const int istep = rev ? -TC : TC;
   // k = last step below e_jb, clamped to an interval
-  pos_t eb = sedge[jb];
+  pos_t eb = sedge[DR_IDX(jb, B + 1, c.err)];
   const int n_below = count_prefix(
       ((float)eb - (float)tfirst) * ((float)(K - 1) / ((float)tlast - (float)tfirst)) + 1.f, K,
       [&](int i) { return pos(i) < eb; });
   int k = min(max(n_below - 1, 0), K - 2);
-  const float I0 = biased(ip[0]);
+  const float I0 = biased(*DR_PTR(ip, simg, Kpad * TC, c.err));
   OutT *o = o0 + (size_t)jb * plane;
   if constexpr (kFx) {
     // Walk state: t0 = t_k, t1 = t_{k+1} (pp points at t1), the image of
@@ -898,18 +929,19 @@ __device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint1
     // bin advances at most once when the plan found every step at least as
     // long as every bin (kOneAdv), else as often as needed.
     const int32_t *pp = spos + (k + 1) * TC + lc;
-    int32_t t0 = pp[-TC], t1 = *pp;
+    int32_t t0 = *DR_PTR(pp - TC, spos, K * TC, c.err), t1 = *DR_PTR(pp, spos, K * TC, c.err);
     const uint16_t *ipn = ip + (k + 1) * istep;
-    float Ik1 = biased(*ipn);
-    const float Ik = biased(ipn[-istep]);
+    const int n_simg = Kpad * TC;
+    float Ik1 = biased(*DR_PTR(ipn, simg, n_simg, c.err));
+    const float Ik = biased(*DR_PTR(ipn - istep, simg, n_simg, c.err));
     float base = __fsub_rn(I0, Ik), dI = __fsub_rn(Ik, Ik1);
     float inv = GeoFx::inv_len(t0, t1);
     auto advance = [&]() {
       t0 = t1;
       pp += TC;
-      t1 = *pp;
+      t1 = *DR_PTR(pp, spos, K * TC, c.err);
       ipn += istep;
-      const float In = biased(*ipn);
+      const float In = biased(*DR_PTR(ipn, simg, n_simg, c.err));
       base = __fsub_rn(I0, Ik1);
       dI = __fsub_rn(Ik1, In);
       Ik1 = In;
@@ -925,28 +957,31 @@ __device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint1
       return __fmaf_rn(__fmul_rn(cvt23(max(ec, t0) - t0), inv), dI, base);
     };
     float Fp = F_at(eb);
+    const size_t n_out = plane * B;
     if (acc) {
       for (int j = jb; j < je; ++j, o += plane) {
-        const int32_t e1 = sedge[j + 1];
+        const int32_t e1 = sedge[DR_IDX(j + 1, B + 1, c.err)];
         const float F = F_at(e1);
         const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
-        if (e1 > tfirst && eb < tlast) st_cs(o, __fadd_rn(out_load(o), v));
+        OutT *oc = DR_PTR(o, out, n_out, c.err);
+        if (e1 > tfirst && eb < tlast) st_cs(oc, __fadd_rn(out_load(oc), v));
         Fp = F;
         eb = e1;
       }
     } else {
 #pragma unroll 4
       for (int j = jb; j < je; ++j, o += plane) {
-        const float F = F_at(sedge[j + 1]);
-        st_cs(o, __fmul_rn(sign, __fsub_rn(F, Fp)));
+        const float F = F_at(sedge[DR_IDX(j + 1, B + 1, c.err)]);
+        st_cs(DR_PTR(o, out, n_out, c.err), __fmul_rn(sign, __fsub_rn(F, Fp)));
         Fp = F;
       }
     }
   } else {
     pos_t t0 = pos(k), t1 = pos(k + 1);
     auto inv = Geo::inv_len(t0, t1);
-    float Ik1 = biased(ip[(k + 1) * istep]);
-    const float Ik = biased(ip[k * istep]);
+    const int n_simg = Kpad * TC;
+    float Ik1 = biased(*DR_PTR(ip + (k + 1) * istep, simg, n_simg, c.err));
+    const float Ik = biased(*DR_PTR(ip + k * istep, simg, n_simg, c.err));
     float base = __fsub_rn(I0, Ik), dI = __fsub_rn(Ik, Ik1);
     // F at edge e (k moves forward only): F = f (I_k - I_{k+1}) + (I_0 - I_k)
     auto F_at = [&](pos_t e) {
@@ -956,19 +991,21 @@ __device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint1
         t1 = pos(k + 1);
         inv = Geo::inv_len(t0, t1);
         const float Ikk = Ik1;
-        Ik1 = biased(ip[(k + 1) * istep]);
+        Ik1 = biased(*DR_PTR(ip + (k + 1) * istep, simg, n_simg, c.err));
         base = __fsub_rn(I0, Ikk);
         dI = __fsub_rn(Ikk, Ik1);
       }
       return __fmaf_rn(Geo::frac(e, t0, t1, inv), dI, base);
     };
     float Fp = F_at(eb);
+    const size_t n_out = plane * B;
     if (acc) {
       for (int j = jb; j < je; ++j, o += plane) {
-        const pos_t e1 = sedge[j + 1];
+        const pos_t e1 = sedge[DR_IDX(j + 1, B + 1, c.err)];
         const float F = F_at(e1);
         const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
-        if (e1 > tfirst && eb < tlast) st_cs(o, __fadd_rn(out_load(o), v));
+        OutT *oc = DR_PTR(o, out, n_out, c.err);
+        if (e1 > tfirst && eb < tlast) st_cs(oc, __fadd_rn(out_load(oc), v));
         Fp = F;
         eb = e1;
       }
@@ -977,10 +1014,10 @@ __device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint1
       // needed for the zero rule
 #pragma unroll 2
       for (int j = jb; j < je; ++j, o += plane) {
-        const pos_t e1 = sedge[j + 1];
+        const pos_t e1 = sedge[DR_IDX(j + 1, B + 1, c.err)];
         const float F = F_at(e1);
         const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
-        st_cs(o, eb < tlast ? v : zero);
+        st_cs(DR_PTR(o, out, n_out, c.err), eb < tlast ? v : zero);
         Fp = F;
         eb = e1;
       }
@@ -1039,14 +1076,14 @@ __device__ __forceinline__ bool pixels_poly_tile(const CUtensorMap *tmap, const 
   stage_tile<kTma>(tmap, img, simg, bar, c, t, row, c0);
   for (int k = tid; k < K; k += NT) {
     const StepC s = c.stp[k];
-    sstep[k] = make_int2(__float_as_int(s.dz), s.zfx);
+    sstep[DR_IDX(k, K, c.err)] = make_int2(__float_as_int(s.dz), s.zfx);
   }
-  for (int j = tid; j <= B; j += NT) sedge[j] = c.efx[j];
+  for (int j = tid; j <= B; j += NT) sedge[DR_IDX(j, B + 1, c.err)] = c.efx[j];
   const GroupPoly gp = as_poly(c.grp[valid ? row * c.W + c0 + lc : row * c.W + c0]);
   __syncthreads();  // also makes the mbarrier initialisation visible
   // position of step k: depth_fx_poly, operation for operation
   auto pos = [&](int k) {
-    const int2 st = sstep[k];
+    const int2 st = sstep[DR_IDX(k, K, c.err)];
     const float d = __int_as_float(st.x);
     const float r = __fmaf_rn(__fmaf_rn(__fmaf_rn(gp.c3, d, gp.c2), d, gp.c1), d, gp.c0);
     return (int32_t)((uint32_t)st.y + (uint32_t)gp.q0fx +
@@ -1074,9 +1111,9 @@ __device__ __forceinline__ bool pixels_poly_tile(const CUtensorMap *tmap, const 
   const int32_t lo_d = group_min(valid ? tfirst : sedge[B], SW);
   const int32_t hi_d = group_max(valid ? tlast : e0, SW);
   const int n_le = count_prefix(((float)lo_d - (float)e0) * bins_per_pos + 1.f, B + 1,
-                                [&](int i) { return !(sedge[i] > lo_d); });
+                                [&](int i) { return !(sedge[DR_IDX(i, B + 1, c.err)] > lo_d); });
   const int n_lt = count_prefix(((float)hi_d - (float)e0) * bins_per_pos + 1.f, B + 1,
-                                [&](int i) { return sedge[i] < hi_d; });
+                                [&](int i) { return sedge[DR_IDX(i, B + 1, c.err)] < hi_d; });
   const int jlo = min(max(n_le - 1, 0), B);
   const int2 sp = make_int2(jlo, max(min(n_lt, B), jlo));
   if constexpr (kTma) {
@@ -1096,12 +1133,13 @@ __device__ __forceinline__ bool pixels_poly_tile(const CUtensorMap *tmap, const 
       for (int i = share * SW + sl; i < nz * kVec; i += G * SW) {
         const int z = i >> kvl, part = i & (kVec - 1);
         const int j = z < sp.x ? z : z - sp.x + sp.y;
-        st_cs_u4(os + (size_t)j * plane + part * kPer, zv);
+        st_cs_u4(DR_PTR(os + (size_t)j * plane + part * kPer, out, plane * B - (kPer - 1), c.err),
+                 zv);
       }
     } else if (valid) {
       for (int z = share; z < nz; z += G) {
         const int j = z < sp.x ? z : z - sp.x + sp.y;
-        st_cs(os + (size_t)j * plane + sl, zero);
+        st_cs(DR_PTR(os + (size_t)j * plane + sl, out, plane * B, c.err), zero);
       }
     }
   }
@@ -1113,7 +1151,7 @@ __device__ __forceinline__ bool pixels_poly_tile(const CUtensorMap *tmap, const 
   const bool rev = c.reverse != 0;
   const uint16_t *ip = simg + (rev ? (K - 1) * TC : 0) + lc;
   const int istep = rev ? -TC : TC;
-  int32_t eb = sedge[jb];
+  int32_t eb = sedge[DR_IDX(jb, B + 1, c.err)];
   const int n_below = count_prefix(
       ((float)eb - (float)tfirst) * ((float)(K - 1) / ((float)tlast - (float)tfirst)) + 1.f, K,
       [&](int i) { return pos(i) < eb; });
@@ -1122,17 +1160,18 @@ __device__ __forceinline__ bool pixels_poly_tile(const CUtensorMap *tmap, const 
   // k + 1 at ipn, base = I_0 - I_k, dI = I_k - I_{k+1}
   int k1 = k + 1;
   int32_t t0 = pos(k), t1 = pos(k1);
-  const float I0 = biased(ip[0]);
+  const int n_simg = Kpad * TC;
+  const float I0 = biased(*DR_PTR(ip, simg, n_simg, c.err));
   const uint16_t *ipn = ip + k1 * istep;
-  float Ik1 = biased(*ipn);
-  const float Ik = biased(ipn[-istep]);
+  float Ik1 = biased(*DR_PTR(ipn, simg, n_simg, c.err));
+  const float Ik = biased(*DR_PTR(ipn - istep, simg, n_simg, c.err));
   float base = __fsub_rn(I0, Ik), dI = __fsub_rn(Ik, Ik1);
   float inv = GeoFx::inv_len(t0, t1);
   auto advance = [&]() {
     t0 = t1;
     t1 = pos(++k1);
     ipn += istep;
-    const float In = biased(*ipn);
+    const float In = biased(*DR_PTR(ipn, simg, n_simg, c.err));
     base = __fsub_rn(I0, Ik1);
     dI = __fsub_rn(Ik1, In);
     Ik1 = In;
@@ -1148,20 +1187,22 @@ __device__ __forceinline__ bool pixels_poly_tile(const CUtensorMap *tmap, const 
   };
   OutT *o = out + (size_t)row * c.W + c0 + lc + (size_t)jb * plane;
   float Fp = F_at(eb);
+  const size_t n_out = plane * B;
   if (acc) {
     for (int j = jb; j < je; ++j, o += plane) {
-      const int32_t e1 = sedge[j + 1];
+      const int32_t e1 = sedge[DR_IDX(j + 1, B + 1, c.err)];
       const float F = F_at(e1);
       const float v = __fmul_rn(sign, __fsub_rn(F, Fp));
-      if (e1 > tfirst && eb < tlast) st_cs(o, __fadd_rn(out_load(o), v));
+      OutT *oc = DR_PTR(o, out, n_out, c.err);
+      if (e1 > tfirst && eb < tlast) st_cs(oc, __fadd_rn(out_load(oc), v));
       Fp = F;
       eb = e1;
     }
   } else {
 #pragma unroll 4
     for (int j = jb; j < je; ++j, o += plane) {
-      const float F = F_at(sedge[j + 1]);
-      st_cs(o, __fmul_rn(sign, __fsub_rn(F, Fp)));
+      const float F = F_at(sedge[DR_IDX(j + 1, B + 1, c.err)]);
+      st_cs(DR_PTR(o, out, n_out, c.err), __fmul_rn(sign, __fsub_rn(F, Fp)));
       Fp = F;
     }
   }
@@ -1208,10 +1249,12 @@ struct BatchScan {
   int kind;                // kBatchRows / kBatchPixelsOneAdv / kBatchPixels
 };
 
-template <class OutT>
-__global__ void __launch_bounds__(512, 1) batch_kernel(const BatchScan *__restrict__ scans,
-                                                       int nscans, long long n_items,
-                                                       unsigned long long *counter) {
+// kPolyOnly: every scan is a per-pixel plan of the polynomial form; this
+// instance holds only that tile, which fits three 512-thread CTAs per SM.
+template <class OutT, bool kPolyOnly>
+__global__ void __launch_bounds__(512, kPolyOnly ? 3 : 1)
+    batch_kernel(const BatchScan *__restrict__ scans, int nscans, long long n_items,
+                 unsigned long long *counter) {
   extern __shared__ __align__(128) unsigned char smem[];
   long long *slot = reinterpret_cast<long long *>(smem + 16);
   int *sscan = reinterpret_cast<int *>(smem + 24);
@@ -1238,7 +1281,13 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(const BatchScan *__restri
     const int c0 = (int)(local % S.tiles_per_row) * S.t.tile_cols;
     OutT *const o = reinterpret_cast<OutT *>(S.out);
     bool ok;
-    if (S.kind == kBatchRows)
+    if constexpr (kPolyOnly) {
+      ok = S.kind == kBatchPixelsPolyOneAdv
+               ? pixels_poly_tile<OutT, true, true>(&S.tmap, S.img, o, S.c, S.t, row, c0, smem,
+                                                    parity)
+               : pixels_poly_tile<OutT, true, false>(&S.tmap, S.img, o, S.c, S.t, row, c0, smem,
+                                                     parity);
+    } else if (S.kind == kBatchRows)
       ok = rows_tile<GeoFx, OutT, true, 4>(&S.tmap, S.img, o, S.c, S.t, row, c0, smem, parity);
     else if (S.kind == kBatchPixelsPolyOneAdv)
       ok = pixels_poly_tile<OutT, true, true>(&S.tmap, S.img, o, S.c, S.t, row, c0, smem,

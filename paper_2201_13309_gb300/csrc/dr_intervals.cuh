@@ -108,12 +108,12 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
         const int k2 = min(k + S, K - 1);
         pos_t d0, d1;
         Geo::depth2(g, steps[k], steps[k2], c, d0, d1);
-        spos[k * TC + lc] = d0;
-        if (k + S < K) spos[(k + S) * TC + lc] = d1;
+        spos[DR_IDX(k * TC + lc, K * TC, c.err)] = d0;
+        if (k + S < K) spos[DR_IDX((k + S) * TC + lc, K * TC, c.err)] = d1;
       }
     }
   }
-  for (int j = tid; j <= B; j += NT) sedge[j] = Geo::edge(c, j);
+  for (int j = tid; j <= B; j += NT) sedge[DR_IDX(j, B + 1, c.err)] = Geo::edge(c, j);
   __syncthreads();  // also makes the mbarrier initialisation visible
   if constexpr (kTma) {
     const bool late = !mbar_wait_bounded(bar, 0, c.err);
@@ -133,15 +133,15 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
     int g = (int)fminf(fmaxf((float)(x - e0) * inv_w + 1.f, 0.f), (float)(B + 1));
 #pragma unroll
     for (int it = 0; it < 3; ++it) {
-      const bool below_ok = g == 0 || sedge[g - 1] <= x;   // e_{g-1} <= x
-      const bool above_ok = g == B + 1 || sedge[g] > x;    // e_g > x
+      const bool below_ok = g == 0 || sedge[DR_IDX(g - 1, B + 1, c.err)] <= x;  // e_{g-1} <= x
+      const bool above_ok = g == B + 1 || sedge[DR_IDX(g, B + 1, c.err)] > x;   // e_g > x
       if (below_ok && above_ok) return g;
       g += below_ok ? 1 : -1;
     }
     int lo = 0, hi = B + 1;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (sedge[mid] <= x) lo = mid + 1; else hi = mid;
+      if (sedge[DR_IDX(mid, B + 1, c.err)] <= x) lo = mid + 1; else hi = mid;
     }
     return lo;
   };
@@ -150,30 +150,37 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
     const int wb1 = min(wb0 + window, B);
     const int nwin = (wb1 - wb0) * TC;  // even: 8 accumulators per bin
     for (int i = tid; i < nwin / 2; i += NT)
-      reinterpret_cast<ulonglong2 *>(acc)[i] = make_ulonglong2(0ull, 0ull);
+      reinterpret_cast<ulonglong2 *>(acc)[DR_IDX(i, window * TC / 2, c.err)] =
+          make_ulonglong2(0ull, 0ull);
     __syncthreads();
     const pos_t ewlo = sedge[wb0], ewhi = sedge[wb1];
     // intervals m = s4, s4 + S, ... of pixel lc
     for (int m = s4; m < K - 1 && lc < ncols; m += S) {
       const int ia = rev ? K - 1 - m : m, ib = rev ? K - 2 - m : m + 1;
-      const int dI = (int)simg[ia * TC + lc] - (int)simg[ib * TC + lc];
+      const int n_simg = Kpad * TC;
+      const int dI = (int)simg[DR_IDX(ia * TC + lc, n_simg, c.err)] -
+                     (int)simg[DR_IDX(ib * TC + lc, n_simg, c.err)];
       if (dI == 0) continue;
-      const pos_t a = spos[m * TC + lc], b = spos[(m + 1) * TC + lc];
+      const pos_t a = spos[DR_IDX(m * TC + lc, K * TC, c.err)],
+                  b = spos[DR_IDX((m + 1) * TC + lc, K * TC, c.err)];
       const pos_t lo = a < b ? a : b, hi = a < b ? b : a;
       if (lo >= ewhi || hi < ewlo) continue;  // nothing in this window
       const int u = count_le(lo);
       if (!(hi > lo)) {  // zero length: the bin [e_j, e_{j+1}) holding lo
         const int j = u - 1;
         if (j >= wb0 && j < wb1)
-          atomicAdd(&acc[(j - wb0) * TC + lc], (unsigned long long)((long long)dI * (1ll << 30)));
+          atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
+                    (unsigned long long)((long long)dI * (1ll << 30)));
         continue;
       }
       const auto inv = iv_inv_len(lo, hi);
       int j = max(u - 1, wb0);
-      long long p0 = iv_phi(sedge[j], lo, hi, inv, dI);
-      for (; j < wb1 && sedge[j] < hi; ++j) {
-        const long long p1 = iv_phi(sedge[j + 1], lo, hi, inv, dI);
-        if (p1 != p0) atomicAdd(&acc[(j - wb0) * TC + lc], (unsigned long long)(p1 - p0));
+      long long p0 = iv_phi(sedge[DR_IDX(j, B + 1, c.err)], lo, hi, inv, dI);
+      for (; j < wb1 && sedge[DR_IDX(j, B + 1, c.err)] < hi; ++j) {
+        const long long p1 = iv_phi(sedge[DR_IDX(j + 1, B + 1, c.err)], lo, hi, inv, dI);
+        if (p1 != p0)
+          atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
+                    (unsigned long long)(p1 - p0));
         p0 = p1;
       }
     }
@@ -183,9 +190,12 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
       // 4 pixels per thread: two 16-byte shared loads, one vector store
       for (int q = tid; q < nwin / 4; q += NT) {
         const int jj = q >> 1, half = q & 1;
-        const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(acc)[2 * q];
-        const ulonglong2 b = reinterpret_cast<const ulonglong2 *>(acc)[2 * q + 1];
-        OutT *o = out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + 4 * half;
+        const ulonglong2 a =
+            reinterpret_cast<const ulonglong2 *>(acc)[DR_IDX(2 * q, window * TC / 2, c.err)];
+        const ulonglong2 b =
+            reinterpret_cast<const ulonglong2 *>(acc)[DR_IDX(2 * q + 1, window * TC / 2, c.err)];
+        OutT *o = DR_PTR(out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + 4 * half,
+                         out, plane * B - 3, c.err);
         st_cs4(o, __fmul_rn(sign, iv_value((long long)a.x)),
                __fmul_rn(sign, iv_value((long long)a.y)),
                __fmul_rn(sign, iv_value((long long)b.x)),
@@ -195,8 +205,9 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
       for (int i = tid; i < nwin; i += NT) {
         const int jj = i / TC, px = i - jj * TC;
         if (px >= ncols) continue;
-        OutT *o = out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + px;
-        const float v = __fmul_rn(sign, iv_value((long long)acc[i]));
+        OutT *o = DR_PTR(out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + px, out,
+                         plane * B, c.err);
+        const float v = __fmul_rn(sign, iv_value((long long)acc[DR_IDX(i, window * TC, c.err)]));
         st_cs(o, acc_out ? __fadd_rn(out_load(o), v) : v);
       }
     }

@@ -136,7 +136,9 @@ constexpr int32_t kMaxStepUnits = 1 << 23;
 __host__ __device__ inline int row_table_entries(int B) { return (B + 2 + 1) & ~1; }
 
 // Error codes written to the device error word.
-enum : int32_t { kDevOk = 0, kDevTmaTimeout = 1 };
+// The bounds-checked build (DR_CHECK_BOUNDS) writes kDevBounds | (line << 4),
+// the device-source line of the first index found out of range.
+enum : int32_t { kDevOk = 0, kDevTmaTimeout = 1, kDevBounds = 2 };
 
 struct Tuning {
   int tile_cols;           // pixels per CTA along the row

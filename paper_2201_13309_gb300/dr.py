@@ -14,7 +14,9 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdr.so")
+# DR_LIBRARY selects another build of the same library (the bounds-checked
+# test build, libdr_checked.so); the default is the in-tree libdr.so
+LIB_PATH = os.environ.get("DR_LIBRARY") or os.path.join(HERE, "libdr.so")
 
 DR_OK = 0
 STATUS = {0: "DR_OK", 1: "DR_ERR_INVALID_ARG", 2: "DR_ERR_GEOMETRY",

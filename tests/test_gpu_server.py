@@ -58,7 +58,8 @@ def test_same_result_alone_and_in_the_mix():
         srv.wait(rid, timeout=60)
         mixed.append(_result(srv, rid, sc))
         _, times = srv.fetch(rid)
-        assert (times["submitted"] <= times["admitted"] <= times["planned"] <= times["uploaded"]
+        # plans are built ahead of admission by the planner threads
+        assert (times["submitted"] <= times["planned"] <= times["admitted"] <= times["uploaded"]
                 <= times["done"])
     for rid in ids:
         srv.release(rid)
