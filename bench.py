@@ -605,7 +605,8 @@ def run_served(args, dev):
                 sp = specs[i]
                 parts.append((sp.P * sp.K * 2, t["planned"] - t["submitted"],
                               t["admitted"] - t["submitted"], t["uploaded"] - t["admitted"],
-                              t["done"] - t["uploaded"]))
+                              t["done"] - t["uploaded"], t["issued"] - t["admitted"],
+                              t["copy"]))
                 if trace is not None:
                     trace.write(json.dumps(dict(t, rate=rate, i=i, rows=sp.geom["rows"],
                                                 cols=sp.geom["cols"], K=sp.K, B=sp.B)) + "\n")
@@ -633,7 +634,7 @@ def run_served(args, dev):
         big = in_gb >= np.percentile(in_gb, 90)
         # phases from arrival: plan ready, admitted (plan ready, slot and
         # memory free), upload done (after earlier uploads), kernel done
-        names = ("plan_wait", "queue", "upload", "kernel")
+        names = ("plan_wait", "queue", "upload", "kernel", "issue", "copy")
         results.append({"offered_scans_per_s": rate, "scans": args.served_scans,
                         "achieved_scans_per_s": args.served_scans / wall,
                         "plans_built": srv.stats()["plans_built"] - built0,

@@ -350,9 +350,12 @@ enum { DR_REQ_QUEUED = 0, DR_REQ_UPLOADING = 1, DR_REQ_RUNNING = 2, DR_REQ_DONE 
  * planned (the request's plan was ready: found in the cache at submission,
  * or built by a planner thread while the request waited), admitted (plan
  * ready, slot and memory reserved), uploaded (the upload, which waits behind
- * earlier uploads, is done), done (kernel done). */
+ * earlier uploads, is done, as its host callback saw it), done (kernel done,
+ * as its host callback saw it); issued (the upload was queued on the upload
+ * stream) and copy (the device's duration of the upload copy itself, from
+ * CUDA events; -1 if unknown). */
 typedef struct {
-  double submitted, admitted, planned, uploaded, done;
+  double submitted, admitted, planned, uploaded, done, issued, copy;
 } dr_request_times;
 
 typedef struct {

@@ -129,7 +129,8 @@ struct dr_server {
   unsigned char *base = nullptr;
   Arena arena;
   std::vector<cudaStream_t> streams;   // one compute stream per slot
-  std::vector<cudaEvent_t> up_done;    // per slot: its request's upload is done
+  std::vector<cudaEvent_t> up_start;   // per slot: before its request's upload (timing)
+  std::vector<cudaEvent_t> up_done;    // per slot: its request's upload is done (timing)
   cudaStream_t up = nullptr;           // uploads, one at a time in admission order
   std::vector<int> slot_busy;
   std::mutex mu;
@@ -174,11 +175,15 @@ std::string plan_key(const Request &r) {
 }
 
 // Host callbacks (CUDA's callback thread: no CUDA calls in here).
+// The upload's callback can run after the kernel's (both only note times):
+// uploaded is then the done time.
 void CUDART_CB on_uploaded(void *arg) {
   Request *r = static_cast<Request *>(arg);
   std::lock_guard<std::mutex> lk(r->srv->mu);
-  r->t.uploaded = now_s() - r->srv->t0;
-  if (r->state == DR_REQ_UPLOADING) r->state = DR_REQ_RUNNING;
+  if (r->state == DR_REQ_UPLOADING) {
+    r->t.uploaded = now_s() - r->srv->t0;
+    r->state = DR_REQ_RUNNING;
+  }
 }
 
 void CUDART_CB on_done(void *arg) {
@@ -187,6 +192,7 @@ void CUDART_CB on_done(void *arg) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r->t.done = now_s() - s->t0;
+    if (r->state == DR_REQ_UPLOADING) r->t.uploaded = r->t.done;
     r->state = DR_REQ_DONE;
     s->finished.push_back(r);
     s->completed++;
@@ -267,15 +273,30 @@ void scheduler(dr_server_t *s) {
   std::unique_lock<std::mutex> lk(s->mu);
   while (!s->stop) {
     bool progress = false;
-    // kernels that finished: their image blocks and slots go back
-    for (Request *r : s->finished) {
-      s->arena.release(r->img_off, r->img_bytes);
-      r->img_off = Arena::kNone;
-      s->slot_busy[r->slot] = 0;
-      r->done_seen = true;
+    // kernels that finished: the device time of their uploads (the slot's
+    // events, read without the lock), then their image blocks and slots go back
+    if (!s->finished.empty()) {
+      std::vector<Request *> fin;
+      fin.swap(s->finished);
+      lk.unlock();
+      std::vector<float> copy_ms(fin.size(), -1.f);
+      for (size_t i = 0; i < fin.size(); ++i)
+        if (cudaEventElapsedTime(&copy_ms[i], s->up_start[fin[i]->slot],
+                                 s->up_done[fin[i]->slot]) != cudaSuccess) {
+          cudaGetLastError();
+          copy_ms[i] = -1.f;
+        }
+      lk.lock();
+      for (size_t i = 0; i < fin.size(); ++i) {
+        Request *r = fin[i];
+        r->t.copy = copy_ms[i] >= 0.f ? copy_ms[i] * 1e-3 : -1.0;
+        s->arena.release(r->img_off, r->img_bytes);
+        r->img_off = Arena::kNone;
+        s->slot_busy[r->slot] = 0;
+        r->done_seen = true;
+      }
       progress = true;
     }
-    s->finished.clear();
     if (progress) s->cv_done.notify_all();
     // choose admissions in arrival order while the head's plan is ready and
     // a slot and memory are free
@@ -340,13 +361,18 @@ void scheduler(dr_server_t *s) {
       void *d_out = s->base + r->out_off;
       if (st == DR_OK) {
         // uploads share the host link: one at a time, in admission order, so
-        // each finishes as early as possible; the slot's kernel waits for it
-        cudaError_t e = cudaMemcpyAsync(d_img, r->h_images, r->img_bytes,
-                                        cudaMemcpyHostToDevice, s->up);
-        // the event follows the callback, so on_uploaded always runs before
-        // the kernel (and its on_done) can start
-        if (e == cudaSuccess) e = cudaLaunchHostFunc(s->up, on_uploaded, r);
+        // each finishes as early as possible; the slot's kernel waits for the
+        // copy itself (its event), not for the host callback that notes the
+        // time, so a late callback does not hold the kernel back
+        cudaError_t e = cudaEventRecord(s->up_start[r->slot], s->up);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(d_img, r->h_images, r->img_bytes, cudaMemcpyHostToDevice, s->up);
+        if (e == cudaSuccess) {
+          std::lock_guard<std::mutex> g(s->mu);
+          r->t.issued = now_s() - s->t0;
+        }
         if (e == cudaSuccess) e = cudaEventRecord(s->up_done[r->slot], s->up);
+        if (e == cudaSuccess) e = cudaLaunchHostFunc(s->up, on_uploaded, r);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, s->up_done[r->slot], 0);
         st = e == cudaSuccess ? dr_reconstruct(r->pe->plan, d_img, d_out, (dr_stream_t)cs)
                               : cuda_fail("server upload", e);
@@ -412,12 +438,14 @@ extern "C" dr_status dr_server_create(const dr_server_options *o, dr_server_t **
   }
   s->arena.reset(o->budget_bytes);
   s->streams.assign(s->opt.slots, nullptr);
+  s->up_start.assign(s->opt.slots, nullptr);
   s->up_done.assign(s->opt.slots, nullptr);
   s->slot_busy.assign(s->opt.slots, 0);
   e = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking);
   for (int i = 0; i < s->opt.slots && e == cudaSuccess; ++i) {
     e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->up_done[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->up_start[i]);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->up_done[i]);
   }
   if (e != cudaSuccess) {
     dr_server_destroy(s);
@@ -463,6 +491,7 @@ extern "C" dr_status dr_server_submit(dr_server_t *s, const dr_geometry *g, cons
   r->h_images = h_images;
   r->img_bytes = P * K * 2;
   r->out_bytes = P * B * 4;
+  r->t.copy = -1.0;
   r->key = plan_key(*r);
   r->srv = s;
   {
@@ -536,12 +565,15 @@ extern "C" dr_status dr_server_fetch(dr_server_t *s, uint64_t id, const void **d
     set_error("dr_server_fetch: null server");
     return DR_ERR_INVALID_ARG;
   }
-  std::lock_guard<std::mutex> lk(s->mu);
+  std::unique_lock<std::mutex> lk(s->mu);
   Request *r = find(s, id);
   if (!r) {
     set_error("dr_server_fetch: unknown request %llu", (unsigned long long)id);
     return DR_ERR_INVALID_ARG;
   }
+  // a done request's upload time is read by the scheduler right after
+  while (r->state == DR_REQ_DONE && !r->done_seen)
+    s->cv_done.wait_for(lk, std::chrono::milliseconds(1));
   if (times) *times = r->t;
   if (r->state == DR_REQ_FAILED) {
     set_error("request %llu failed: %s", (unsigned long long)id, dr_status_string(r->status));
@@ -643,6 +675,8 @@ extern "C" void dr_server_destroy(dr_server_t *s) {
       cudaStreamSynchronize(st);
       cudaStreamDestroy(st);
     }
+  for (auto ev : s->up_start)
+    if (ev) cudaEventDestroy(ev);
   for (auto ev : s->up_done)
     if (ev) cudaEventDestroy(ev);
   for (auto &kv : s->reqs) delete kv.second;

@@ -100,7 +100,8 @@ class ServerOptions(ctypes.Structure):
 class RequestTimes(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_double), ("admitted", ctypes.c_double),
                 ("planned", ctypes.c_double), ("uploaded", ctypes.c_double),
-                ("done", ctypes.c_double)]
+                ("done", ctypes.c_double), ("issued", ctypes.c_double),
+                ("copy", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):

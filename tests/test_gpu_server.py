@@ -59,8 +59,9 @@ def test_same_result_alone_and_in_the_mix():
         mixed.append(_result(srv, rid, sc))
         _, times = srv.fetch(rid)
         # plans are built ahead of admission by the planner threads
-        assert (times["submitted"] <= times["planned"] <= times["admitted"] <= times["uploaded"]
-                <= times["done"])
+        assert (times["submitted"] <= times["planned"] <= times["admitted"] <= times["issued"]
+                <= times["uploaded"] <= times["done"])
+        assert 0 < times["copy"] <= times["done"] - times["admitted"]
     for rid in ids:
         srv.release(rid)
     st = srv.stats()
