@@ -533,6 +533,28 @@ def run_batched(args, dev, specs=None):
     }
 
 
+def hugepage_pinned(shape, keep):
+    """An int16 host tensor in anonymous memory advised for transparent huge
+    pages and page-locked with cudaHostRegister (instead of cudaHostAlloc);
+    the mapping is appended to keep, which must outlive the tensor."""
+    import ctypes
+    import mmap
+
+    import torch
+
+    n = int(np.prod(shape)) * 2
+    m = mmap.mmap(-1, n, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+    if hasattr(mmap, "MADV_HUGEPAGE"):
+        m.madvise(mmap.MADV_HUGEPAGE)
+    buf = (ctypes.c_uint8 * n).from_buffer(m)
+    ctypes.memset(buf, 0, n)  # touch every page before registering
+    err = torch.cuda.cudart().cudaHostRegister(ctypes.addressof(buf), n, 0)
+    if int(err) != 0:
+        raise RuntimeError(f"cudaHostRegister failed ({err})")
+    keep.append((m, buf))
+    return torch.frombuffer(buf, dtype=torch.int16).view(shape)
+
+
 def run_served(args, dev):
     """Poisson arrival streams of scans from the uneven-batch distribution into
     the server (admission against an HBM budget, pinned uploads overlapped on
@@ -553,6 +575,7 @@ def run_served(args, dev):
     from tests.gen import synth
 
     placement = near_gpu(dev)
+    keep = []  # the mappings behind hugepage-pinned buffers
     kmax = 801
     buffers, up_gbs = {}, {}
     for i, (rows, cols) in enumerate(synth.ROI_CHOICES):
@@ -564,7 +587,8 @@ def run_served(args, dev):
         img = synth.device_spot_images(geom, wires, scat, seed=2000 + i, background=20.0,
                                        device=dev)
         with placement:
-            h = torch.empty(img.shape, dtype=torch.int16, pin_memory=True)
+            h = (hugepage_pinned(img.shape, keep) if args.served_pin == "hugepage"
+                 else torch.empty(img.shape, dtype=torch.int16, pin_memory=True))
             h.copy_(img)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -688,7 +712,7 @@ def run_served(args, dev):
     mean_in = float(np.mean([sp.P * sp.K * 2 for sp in sat_specs])) / 1e9
     return {"mode": "served", "metric": "scans/s and p50/p99 latency (arrival -> result on device)",
             "budget_GB": args.budget_gb, "slots": args.slots,
-            "pinned_upload_GBps": up_gbs, "alloc_cpus": placement.cpus,
+            "pin": args.served_pin, "pinned_upload_GBps": up_gbs, "alloc_cpus": placement.cpus,
             "mean_input_GB": mean_in, "rates": results,
             "plan_cache": {"plans_built": st["plans_built"], "failed": st["failed"]},
             "saturation": {"scans": n_sat, "server_scans_per_s": n_sat / t_srv,
@@ -760,6 +784,9 @@ def main():
     ap.add_argument("--rates", default="5,20,50")
     ap.add_argument("--served-scans", type=int, default=1000)
     ap.add_argument("--saturation-scans", type=int, default=96)
+    ap.add_argument("--served-pin", default="torch", choices=["torch", "hugepage"],
+                    help="served: pinned image pool from cudaHostAlloc (torch) or from "
+                         "huge-page memory registered with cudaHostRegister")
     ap.add_argument("--served-trace", default="",
                     help="served: write every request's timestamps to this file")
     ap.add_argument("--slots", type=int, default=4)

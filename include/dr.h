@@ -285,8 +285,11 @@ typedef struct dr_batch dr_batch_t;
 /* Optional batch settings; null means all zero (defaults). */
 typedef struct {
   int32_t ctas_per_sm;        /* 1 (default, up to 227 KB of shared memory per
-                                 CTA) or 2 (up to 113 KB each: narrower tiles,
-                                 two CTAs overlapping on each SM) */
+                                 CTA), 2 (up to 113 KB each: narrower tiles,
+                                 two CTAs overlapping on each SM) or 3 (up to
+                                 75 KB each; reached with 512-thread CTAs when
+                                 every job is a per-pixel plan of the
+                                 polynomial form) */
   int32_t max_tile_cols;      /* cap on each job's tile width; 0 = the plan's */
   int32_t threads;            /* threads per CTA: 256 or 512 (0 = 512) */
   int32_t reserved;

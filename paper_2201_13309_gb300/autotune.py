@@ -15,7 +15,7 @@ import threading
 from . import dr
 
 ROWS_CANDIDATES = ((128, 16), (128, 8), (256, 8), (256, 4), (64, 16), (128, 4))
-PIXELS_CANDIDATES = ((32, 16), (16, 32), (16, 16), (8, 64), (32, 8), (64, 8))
+PIXELS_CANDIDATES = ((32, 16), (16, 32), (16, 16), (8, 64), (32, 8), (64, 8), (128, 4), (64, 4))
 
 _lock = threading.Lock()
 
@@ -128,7 +128,8 @@ def tuned_plan(geom, wires, edges, images, **kw):
 
 
 # (CTAs per SM, tile-width cap, threads per CTA)
-BATCH_CANDIDATES = ((1, 0, 256), (1, 0, 512), (2, 0, 512), (2, 0, 256), (2, 64, 512))
+BATCH_CANDIDATES = ((1, 0, 256), (1, 0, 512), (2, 0, 512), (2, 0, 256), (2, 64, 512),
+                    (3, 0, 512))
 
 
 def tuned_batch(jobs, reps=2, stream=None):

@@ -65,9 +65,9 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
   dr_batch_options opt;
   std::memset(&opt, 0, sizeof(opt));
   if (opt_in) opt = *opt_in;
-  if (opt.ctas_per_sm < 0 || opt.ctas_per_sm > 2 || opt.max_tile_cols < 0 ||
+  if (opt.ctas_per_sm < 0 || opt.ctas_per_sm > 3 || opt.max_tile_cols < 0 ||
       (opt.threads != 0 && opt.threads != 256 && opt.threads != 512)) {
-    set_error("dr_batch_create: ctas_per_sm must be 0, 1 or 2 and threads 0, 256 or 512");
+    set_error("dr_batch_create: ctas_per_sm must be 0..3 and threads 0, 256 or 512");
     return DR_ERR_INVALID_ARG;
   }
   const int nthreads = opt.threads ? opt.threads : kBatchThreads;

@@ -774,6 +774,43 @@ __device__ __forceinline__ T group_max(T v, int width) {
   return v;
 }
 
+// The bins of a slab outside its data span [sp.x, sp.y) are zero for all
+// its pixels.  A full slab whose rows start on 16 bytes stores them with
+// 16-byte stores: each of the slab's G * SW threads owns one 16-byte part of
+// a bin row and walks the bins with a fixed stride; otherwise every valid
+// lane stores its own pixel's zeros.
+template <class OutT>
+__device__ __forceinline__ void zero_outside_span(OutT *out, const Consts &c, int row, int c0,
+                                                  int slab, int SW, int share, int sl, int G,
+                                                  int2 sp, int ncols, bool valid, float zero,
+                                                  size_t plane) {
+  constexpr int kPer = 16 / sizeof(OutT);
+  const int B = c.B;
+  OutT *const os = out + (size_t)row * c.W + c0 + slab * SW;
+  if (slab * SW + SW <= ncols && c.W % kPer == 0 && ((uintptr_t)out & 15) == 0) {
+    const uint4 zv = zero_bits<OutT>(zero);
+    const int kVec = SW / kPer, kvl = __ffs(kVec) - 1;  // 16-byte stores per bin row
+    const int q = share * SW + sl;                      // 0 .. G * SW - 1
+    const int part = q & (kVec - 1), first = q >> kvl, stride = (G * SW) >> kvl;
+    const size_t step = (size_t)stride * plane;
+    auto range = [&](int a, int b) {
+      OutT *p = os + (size_t)(a + first) * plane + part * kPer;
+      for (int j = a + first; j < b; j += stride, p += step)
+        st_cs_u4(DR_PTR(p, out, plane * B - (kPer - 1), c.err), zv);
+    };
+    range(0, sp.x);
+    range(sp.y, B);
+  } else if (valid) {
+    auto range = [&](int a, int b) {
+      OutT *p = os + (size_t)(a + share) * plane + sl;
+      for (int j = a + share; j < b; j += G, p += (size_t)G * plane)
+        st_cs(DR_PTR(p, out, plane * B, c.err), zero);
+    };
+    range(0, sp.x);
+    range(sp.y, B);
+  }
+}
+
 // One tile: row `row`, columns c0 .. c0 + tile_cols - 1, all steps and bins.
 // The mbarrier at smem[0] must be initialised (by thread 0 before the call,
 // or earlier with a barrier since); `parity` is its phase for this tile.
@@ -875,29 +912,8 @@ __device__ __forceinline__ bool pixels_tile(const CUtensorMap *tmap, const uint1
   const float sign = c.out_sign, zero = __fmul_rn(sign, 0.f);
   const size_t plane = (size_t)c.H * c.W;
   const bool acc = c.accumulate != 0;
-  // the bins outside the span are zero: a full slab whose rows start on 16
-  // bytes stores them with 16-byte stores, the SW pixels of a bin being
-  // kVec stores, spread over all the slab's threads
-  if (!acc) {
-    constexpr int kPer = 16 / sizeof(OutT);
-    const int kVec = SW / kPer, kvl = __ffs(kVec) - 1;  // 16-byte stores per bin
-    const int nz = B - (sp.y - sp.x);
-    OutT *const os = out + (size_t)row * c.W + c0 + slab * SW;
-    if (slab * SW + SW <= ncols && c.W % kPer == 0 && ((uintptr_t)out & 15) == 0) {
-      const uint4 zv = zero_bits<OutT>(zero);
-      for (int i = share * SW + sl; i < nz * kVec; i += G * SW) {
-        const int z = i >> kvl, part = i & (kVec - 1);
-        const int j = z < sp.x ? z : z - sp.x + sp.y;
-        st_cs_u4(DR_PTR(os + (size_t)j * plane + part * kPer, out, plane * B - (kPer - 1), c.err),
-                 zv);
-      }
-    } else if (valid) {
-      for (int z = share; z < nz; z += G) {
-        const int j = z < sp.x ? z : z - sp.x + sp.y;
-        st_cs(DR_PTR(os + (size_t)j * plane + sl, out, plane * B, c.err), zero);
-      }
-    }
-  }
+  if (!acc)
+    zero_outside_span(out, c, row, c0, slab, SW, share, sl, G, sp, ncols, valid, zero, plane);
   if (!valid) return true;
   OutT *const o0 = out + (size_t)row * c.W + c0 + lc;
   // this share's part of the span
@@ -1123,26 +1139,8 @@ __device__ __forceinline__ bool pixels_poly_tile(const CUtensorMap *tmap, const 
   const float sign = c.out_sign, zero = __fmul_rn(sign, 0.f);
   const size_t plane = (size_t)c.H * c.W;
   const bool acc = c.accumulate != 0;
-  if (!acc) {  // the bins outside the span: zeros, as in pixels_tile
-    constexpr int kPer = 16 / sizeof(OutT);
-    const int kVec = SW / kPer, kvl = __ffs(kVec) - 1;
-    const int nz = B - (sp.y - sp.x);
-    OutT *const os = out + (size_t)row * c.W + c0 + slab * SW;
-    if (slab * SW + SW <= ncols && c.W % kPer == 0 && ((uintptr_t)out & 15) == 0) {
-      const uint4 zv = zero_bits<OutT>(zero);
-      for (int i = share * SW + sl; i < nz * kVec; i += G * SW) {
-        const int z = i >> kvl, part = i & (kVec - 1);
-        const int j = z < sp.x ? z : z - sp.x + sp.y;
-        st_cs_u4(DR_PTR(os + (size_t)j * plane + part * kPer, out, plane * B - (kPer - 1), c.err),
-                 zv);
-      }
-    } else if (valid) {
-      for (int z = share; z < nz; z += G) {
-        const int j = z < sp.x ? z : z - sp.x + sp.y;
-        st_cs(DR_PTR(os + (size_t)j * plane + sl, out, plane * B, c.err), zero);
-      }
-    }
-  }
+  if (!acc)
+    zero_outside_span(out, c, row, c0, slab, SW, share, sl, G, sp, ncols, valid, zero, plane);
   if (!valid) return true;
   const int nd = sp.y - sp.x;
   const int jb = sp.x + (int)((long long)nd * share / G);

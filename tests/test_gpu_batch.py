@@ -140,7 +140,7 @@ def _rotated_scans():
     return [(a, "leading"), (b, "leading"), (c, "trailing")]
 
 
-@pytest.mark.parametrize("per_sm,nt", [(1, 512), (2, 512), (1, 256)])
+@pytest.mark.parametrize("per_sm,nt", [(1, 512), (2, 512), (1, 256), (3, 512)])
 def test_batch_of_rows_and_per_pixel_plans(per_sm, nt):
     """Rows and per-pixel tiles in one persistent launch: every scan bitwise
     as its own launch, and each per-pixel scan against the FP64 oracle."""
