@@ -290,7 +290,9 @@ typedef struct {
                                  75 KB each; reached with 512-thread CTAs when
                                  every job is a per-pixel plan of the
                                  polynomial form) */
-  int32_t max_tile_cols;      /* cap on each job's tile width; 0 = the plan's */
+  int32_t max_tile_cols;      /* cap on each job's tile width (rows tiles:
+                                 multiples of 32; per-pixel tiles: powers
+                                 of two from 8); 0 = the default width */
   int32_t threads;            /* threads per CTA: 256 or 512 (0 = 512) */
   int32_t reserved;
 } dr_batch_options;

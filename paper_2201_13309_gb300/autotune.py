@@ -129,7 +129,7 @@ def tuned_plan(geom, wires, edges, images, **kw):
 
 # (CTAs per SM, tile-width cap, threads per CTA)
 BATCH_CANDIDATES = ((1, 0, 256), (1, 0, 512), (2, 0, 512), (2, 0, 256), (2, 64, 512),
-                    (3, 0, 512))
+                    (3, 0, 512), (3, 64, 512))
 
 
 def tuned_batch(jobs, reps=2, stream=None):

@@ -105,8 +105,8 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
     }
     // tile shape for the batch's CTAs.  Rows tiles: the plan's width (capped
     // by the options), narrowed until the tile fits the per-CTA budget, four
-    // pixels per thread.  Per-pixel tiles: one 32-pixel slab (8 or 16 for
-    // narrower budgets) shared by all the CTA's warps.
+    // pixels per thread.  Per-pixel tiles: one pixel per lane, the bins
+    // shared among nthreads / tile_cols threads per pixel.
     Tuning t = p->tune;
     int smem = 0, lanes = 0;
     if (rows) {
@@ -120,10 +120,14 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
       }
       lanes = t.tile_cols / 4;
     } else {
-      // the polynomial form's tile holds no depth table: 64 columns when
-      // they fit (the plain kernel's tuned width), else narrower
+      // the polynomial form's tile holds no depth table: 128 columns (4
+      // threads per pixel at 512 threads, the standalone kernel's fastest
+      // shape on the full detector) when they fit the budget and the cap,
+      // else narrower
       const bool poly = p->c.depth_mode == kDepthPoly;
-      t.tile_cols = poly && nthreads >= 512 ? 64 : 32;
+      t.tile_cols = poly ? (nthreads >= 512 ? 128 : 64) : 32;
+      while (opt.max_tile_cols >= 8 && t.tile_cols > opt.max_tile_cols && t.tile_cols > 8)
+        t.tile_cols /= 2;  // a power of two: whole 8-, 16- or 32-pixel slabs
       for (;;) {
         choose_chunks(p->K, t.tile_cols, &t.kc, &t.nchunks);
         smem = poly ? pixels_poly_smem_bytes(p->K, t.kc * t.nchunks, p->B, t.tile_cols)
