@@ -200,6 +200,34 @@ def gpu_local_cpus(dev):
         return []
 
 
+def page_nodes(ptr, nbytes, samples=256):
+    """Memory node of `samples` evenly spaced pages of a host buffer (the
+    move_pages system call without a target node reports where each page
+    is), as {node: pages}; None where the call is not available."""
+    import ctypes
+    import platform
+
+    nr = {"aarch64": 239, "x86_64": 279}.get(platform.machine())
+    if nr is None or nbytes <= 0:
+        return None
+    try:
+        libc = ctypes.CDLL(None, use_errno=True)
+        page = os.sysconf("SC_PAGE_SIZE")
+        addrs = sorted({(ptr + i * nbytes // samples) // page * page for i in range(samples)})
+        arr = (ctypes.c_void_p * len(addrs))(*addrs)
+        status = (ctypes.c_int * len(addrs))()
+        rc = libc.syscall(ctypes.c_long(nr), ctypes.c_int(0), ctypes.c_ulong(len(addrs)), arr,
+                          None, status, ctypes.c_int(0))
+        if rc != 0:
+            return None
+        hist = {}
+        for v in status:
+            hist[str(v)] = hist.get(str(v), 0) + 1
+        return hist
+    except Exception:
+        return None
+
+
 class near_gpu:
     """Run the enclosed host allocations on CPUs local to the GPU, so that
     pinned pages are placed in the memory node next to it."""
@@ -577,7 +605,7 @@ def run_served(args, dev):
     placement = near_gpu(dev)
     keep = []  # the mappings behind hugepage-pinned buffers
     kmax = 801
-    buffers, up_gbs = {}, {}
+    buffers, up_gbs, pool_nodes = {}, {}, {}
     for i, (rows, cols) in enumerate(synth.ROI_CHOICES):
         rng = np.random.Generator(np.random.PCG64(3000 + i))
         geom = synth.detector_geometry(rows, cols, (0, 0), synth.FULL_DET, synth.FULL_DET)
@@ -595,6 +623,7 @@ def run_served(args, dev):
         img.copy_(h, non_blocking=True)
         torch.cuda.synchronize()
         up_gbs[f"{rows}x{cols}"] = h.numel() * 2 / (time.perf_counter() - t0) / 1e9
+        pool_nodes[f"{rows}x{cols}"] = page_nodes(h.data_ptr(), h.numel() * 2)
         buffers[(rows, cols)] = h
         del img
     torch.cuda.empty_cache()
@@ -713,6 +742,7 @@ def run_served(args, dev):
     return {"mode": "served", "metric": "scans/s and p50/p99 latency (arrival -> result on device)",
             "budget_GB": args.budget_gb, "slots": args.slots,
             "pin": args.served_pin, "pinned_upload_GBps": up_gbs, "alloc_cpus": placement.cpus,
+            "pool_page_nodes": pool_nodes,
             "mean_input_GB": mean_in, "rates": results,
             "plan_cache": {"plans_built": st["plans_built"], "failed": st["failed"]},
             "saturation": {"scans": n_sat, "server_scans_per_s": n_sat / t_srv,
@@ -722,6 +752,73 @@ def run_served(args, dev):
                          "(ROI 256^2..2048^2 at its own origin, 51-801 steps, 0.5/1/2 um bins "
                          "over +-400 um), so every request builds its plan; images are the "
                          "first K planes of one pinned forward-model scan per ROI size")}
+
+
+def run_link(args, dev):
+    """Host-to-device link under intermittent use: a 2.5 GiB pinned upload
+    every 200 ms (the gaps of a lightly loaded server), first as single
+    copies, then alternating a single copy with the same bytes as 128 MiB
+    pieces, then back-to-back single copies.  Each copy is timed with CUDA
+    events on its stream; nothing else runs in the process meanwhile."""
+    import torch
+
+    n = int(2.5 * (1 << 30))
+    piece = 128 << 20
+    with near_gpu(dev) as place:
+        h = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        h.fill_(1)
+    nodes_before = page_nodes(h.data_ptr(), n)
+    d = torch.empty(n, dtype=torch.uint8, device=dev)
+    st = torch.cuda.Stream(device=dev)
+
+    def timed(pieces):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            for off in range(0, n, n if not pieces else piece):
+                m = min(n - off, piece) if pieces else n
+                d[off:off + m].copy_(h[off:off + m], non_blocking=True)
+            e1.record(st)
+        e1.synchronize()
+        return n / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+    def paced(seconds, kinds):
+        got = {k: [] for k in kinds}
+        t_end, i = time.perf_counter() + seconds, 0
+        while time.perf_counter() < t_end:
+            t = time.perf_counter()
+            k = kinds[i % len(kinds)]
+            i += 1
+            got[k].append(timed(k == "pieces"))
+            time.sleep(max(0.0, 0.2 - (time.perf_counter() - t)))
+        return got
+
+    def summary(v):
+        v = sorted(v)
+        return {"copies": len(v), "GBps_p50": round(v[len(v) // 2], 1),
+                "GBps_p10": round(v[len(v) // 10], 1), "GBps_min": round(v[0], 1)}
+
+    first = paced(args.link_seconds, ["single"])["single"]
+    tenth = max(1, len(first) // 10)
+    mixed = paced(args.link_seconds, ["single", "pieces"])
+    busy = []
+    t_end = time.perf_counter() + 5.0
+    while time.perf_counter() < t_end:
+        busy.append(timed(False))
+    try:
+        online = open("/sys/devices/system/node/online").read().strip()
+    except OSError:
+        online = None
+    return {"mode": "link", "metric": "pinned host-to-device GB/s, 2.5 GiB uploads",
+            "upload_GiB": 2.5, "piece_MiB": 128, "interval_ms": 200,
+            "numa_nodes_online": online, "alloc_cpus": place.cpus,
+            "page_nodes_before": nodes_before,
+            "page_nodes_after": page_nodes(h.data_ptr(), n),
+            "single_first_tenth": summary(first[:tenth]),
+            "single_last_tenth": summary(first[-tenth:]),
+            "mixed_single": summary(mixed["single"]), "mixed_pieces": summary(mixed["pieces"]),
+            "back_to_back_single": summary(busy)}
 
 
 def run_pixels(args, spec, images, dev):
@@ -780,7 +877,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--mode", default="plain",
-                    choices=["plain", "precision", "batched", "served", "pixels"])
+                    choices=["plain", "precision", "batched", "served", "pixels", "link"])
+    ap.add_argument("--link-seconds", type=float, default=60.0,
+                    help="link: seconds of paced uploads in each of its two phases")
     ap.add_argument("--rates", default="5,20,50")
     ap.add_argument("--served-scans", type=int, default=1000)
     ap.add_argument("--saturation-scans", type=int, default=96)
@@ -850,6 +949,10 @@ def main():
     if args.mode == "served":
         if rank == 0:
             print(json.dumps(run_served(args, dev)), flush=True)
+        return 0
+    if args.mode == "link":
+        if rank == 0:
+            print(json.dumps(run_link(args, dev)), flush=True)
         return 0
 
     spec = synth.full_scan_spec(0)
