@@ -16,13 +16,17 @@
 //
 // A CTA owns one row x 8 adjacent pixels x all K steps (image tile staged by
 // TMA as in the other kernels, depths of the 8 pixels in shared memory); a
-// warp covers 4 steps x the 8 pixels.  The bins go through shared-memory
-// windows of `window` int64 accumulators per pixel; the threads take the
-// intervals in turn and add dI * phi(e) on the fixed-point grid 2^-30
-// (Phi(e_{j+1}) - Phi(e_j), so the parts of one interval add up to dI
-// exactly) with shared-memory atomics.  Integer sums do not depend on the
-// order of the atomics, so the result is deterministic.  The window is then
-// written out, 8 pixels of one bin being one 32-byte sector.
+// warp covers 4 steps x the 8 pixels when it evaluates depths, and 4 chunks
+// of consecutive intervals x the 8 pixels when it apportions.  The bins go
+// through shared-memory windows of `window` int64 accumulators per pixel.
+// Each thread splits its chunk into strictly monotone runs (and zero-length
+// intervals) and walks each run once over the bins it spans, adding
+// Phi(e_{j+1}) - Phi(e_j) summed over the run's intervals, Phi(e) =
+// round(dI * phi(e) * 2^30) on the fixed-point grid 2^-30 (so the parts of
+// one interval add up to dI exactly), with shared-memory atomics.  Integer
+// sums do not depend on the order of the atomics, so the result is
+// deterministic and does not depend on how the intervals are grouped.  The
+// window is then written out, 8 pixels of one bin being one 32-byte sector.
 #pragma once
 
 #include "dr_device.cuh"
@@ -146,6 +150,17 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
     return lo;
   };
 
+  // dI of interval m (the step pair it joins, in the plan's travel order)
+  auto step_dI = [&](int m) {
+    const int ia = rev ? K - 1 - m : m, ib = rev ? K - 2 - m : m + 1;
+    const int n_simg = Kpad * TC;
+    return (int)simg[DR_IDX(ia * TC + lc, n_simg, c.err)] -
+           (int)simg[DR_IDX(ib * TC + lc, n_simg, c.err)];
+  };
+  // intervals per chunk: one chunk per thread where K allows; odd, so that
+  // the 4 chunks of a warp start in different banks
+  const int C = ((K - 1 + S - 1) / S) | 1;
+
   for (int wb0 = 0; wb0 < B; wb0 += window) {
     const int wb1 = min(wb0 + window, B);
     const int nwin = (wb1 - wb0) * TC;  // even: 8 accumulators per bin
@@ -154,34 +169,71 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
           make_ulonglong2(0ull, 0ull);
     __syncthreads();
     const pos_t ewlo = sedge[wb0], ewhi = sedge[wb1];
-    // intervals m = s4, s4 + S, ... of pixel lc
-    for (int m = s4; m < K - 1 && lc < ncols; m += S) {
-      const int ia = rev ? K - 1 - m : m, ib = rev ? K - 2 - m : m + 1;
-      const int n_simg = Kpad * TC;
-      const int dI = (int)simg[DR_IDX(ia * TC + lc, n_simg, c.err)] -
-                     (int)simg[DR_IDX(ib * TC + lc, n_simg, c.err)];
-      if (dI == 0) continue;
-      const pos_t a = spos[DR_IDX(m * TC + lc, K * TC, c.err)],
-                  b = spos[DR_IDX((m + 1) * TC + lc, K * TC, c.err)];
-      const pos_t lo = a < b ? a : b, hi = a < b ? b : a;
-      if (lo >= ewhi || hi < ewlo) continue;  // nothing in this window
-      const int u = count_le(lo);
-      if (!(hi > lo)) {  // zero length: the bin [e_j, e_{j+1}) holding lo
-        const int j = u - 1;
-        if (j >= wb0 && j < wb1)
-          atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
-                    (unsigned long long)((long long)dI * (1ll << 30)));
-        continue;
-      }
-      const auto inv = iv_inv_len(lo, hi);
-      int j = max(u - 1, wb0);
-      long long p0 = iv_phi(sedge[DR_IDX(j, B + 1, c.err)], lo, hi, inv, dI);
-      for (; j < wb1 && sedge[DR_IDX(j, B + 1, c.err)] < hi; ++j) {
-        const long long p1 = iv_phi(sedge[DR_IDX(j + 1, B + 1, c.err)], lo, hi, inv, dI);
+    // One strictly monotone run, intervals m .. n - 1, rising (up) or
+    // falling.  Taken in increasing depth, its positions are D(0) < ... <
+    // D(len) and interval i joins D(i) and D(i + 1).  At an edge e the sum
+    // over the run's intervals of Phi_k(e) is P(e) = (sum of dI * 2^30 over
+    // the intervals below e) + Phi of the interval holding e, so a bin gets
+    // P(e_{j+1}) - P(e_j): the same integer as the sum of the intervals'
+    // own differences, with one atomic per bin instead of one per interval.
+    auto iv_run = [&](int m, int n, bool up) {
+      const int len = n - m;
+      auto D = [&](int i) { return spos[DR_IDX((up ? m + i : n - i) * TC + lc, K * TC, c.err)]; };
+      const pos_t lo_run = D(0), hi_run = D(len);
+      if (lo_run >= ewhi || hi_run < ewlo) return;  // nothing in this window
+      int i = 0;
+      pos_t lo_i = lo_run, hi_i = D(1);
+      int dI = step_dI(up ? m : n - 1);
+      auto inv = iv_inv_len(lo_i, hi_i);
+      long long cum = 0;  // dI * 2^30 summed over the intervals below i
+      auto P = [&](pos_t e) {
+        while (i < len && !(e < hi_i)) {
+          cum += (long long)dI * (1ll << 30);
+          if (++i < len) {
+            lo_i = hi_i;
+            hi_i = D(i + 1);
+            dI = step_dI(up ? m + i : n - 1 - i);
+            inv = iv_inv_len(lo_i, hi_i);
+          }
+        }
+        return i < len ? cum + iv_phi(e, lo_i, hi_i, inv, dI) : cum;
+      };
+      int j = max(count_le(lo_run) - 1, wb0);
+      long long p0 = P(sedge[DR_IDX(j, B + 1, c.err)]);
+      for (; j < wb1 && sedge[DR_IDX(j, B + 1, c.err)] < hi_run; ++j) {
+        const long long p1 = P(sedge[DR_IDX(j + 1, B + 1, c.err)]);
         if (p1 != p0)
           atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
                     (unsigned long long)(p1 - p0));
         p0 = p1;
+      }
+    };
+    // chunks of C consecutive intervals of pixel lc, chunk q = s4, s4 + S,
+    // ...; a chunk splits into strictly monotone runs and zero-length
+    // intervals, and each run is walked once over the bins it spans
+    for (int q = s4; q * C < K - 1 && lc < ncols; q += S) {
+      const int m1 = min(q * C + C, K - 1);
+      for (int m = q * C; m < m1;) {
+        const pos_t a = spos[DR_IDX(m * TC + lc, K * TC, c.err)],
+                    b = spos[DR_IDX((m + 1) * TC + lc, K * TC, c.err)];
+        if (!(a < b) && !(b < a)) {  // zero length: the bin [e_j, e_{j+1}) holding a
+          const int dI = step_dI(m);
+          const int j = count_le(a) - 1;
+          if (dI != 0 && j >= wb0 && j < wb1)
+            atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
+                      (unsigned long long)((long long)dI * (1ll << 30)));
+          ++m;
+          continue;
+        }
+        const bool up = a < b;
+        int n = m + 1;  // the run: intervals m .. n - 1
+        for (pos_t prev = b; n < m1; ++n) {
+          const pos_t nx = spos[DR_IDX((n + 1) * TC + lc, K * TC, c.err)];
+          if (up ? !(prev < nx) : !(nx < prev)) break;
+          prev = nx;
+        }
+        iv_run(m, n, up);
+        m = n;
       }
     }
     __syncthreads();

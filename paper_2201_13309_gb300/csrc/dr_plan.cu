@@ -435,8 +435,11 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   // bound of its first dropped term, n / (2 L0) * 5/64 * x^3 / (1 - x), over
   // the ROI (|t| <= T, |Z| <= Zmax, L0 >= Y >= Ymin), carried into the
   // remainder (times R / D) in grid units, below 0.01.  Otherwise exact.
+  // (the interval kernel evaluates the same FP32 positions, so its plans
+  // take the same forms; the check below bounds their distance from FP64)
   int mode = kDepthExact;
-  if (fx_walk && !has_eta && P > 0 && remmax * scale < (double)(1 << 20)) {
+  const bool fx_pos = opt.geom_precision == DR_GEOM_FP32;
+  if (fx_pos && !has_eta && P > 0 && remmax * scale < (double)(1 << 20)) {
     double Zmax = 0.0, Ymin = 1e300;
     for (int cr = 0; cr < 4; ++cr) {
       const double r = (cr & 1) ? H - 1 : 0, cc = (cr & 2) ? W - 1 : 0;

@@ -49,6 +49,26 @@ namespace dr {
 // distance only (the interval kernel takes any order).  res must hold
 // bad = ~0, min_step = tmin = INT32_MAX, max_step = tmax = INT32_MIN and
 // max_dev = 0 before the launch.
+// The FP64 position of (group, step), as depth_f64 solves it, reached by one
+// fixed-point pass from the FP32 position t (grid units).  The pass maps t
+// to z + Q0 + (a + sR dL(t)) / (D - eta); dL has slope below 1 in t and sR
+// is the wire radius, far below D - eta, so the pass shrinks any error in t
+// by that ratio: from a start within a few grid units it lands within a
+// small fraction of a unit of the solution, as depth_f64's passes from its
+// own start do, with two of their five FP64 divisions and one of their two
+// square roots.  inv_scale = 2^-shift.
+__device__ __forceinline__ double depth_f64_from(const GroupD &g, const StepD &s,
+                                                 const Consts &c, double t_units,
+                                                 double inv_scale) {
+  const double z = s.z, Dm = g.D - s.eta;
+  const double a = c.y0d * z + s.eta * (z - g.Z + g.Q0);
+  const double t = t_units * inv_scale + c.origin;
+  const double u = g.Z - t;
+  const double L = sqrt(g.Y2 + u * u);
+  const double dL = t * (t - 2.0 * g.Z) / (L + g.L0);
+  return ((z - c.origin) + g.Q0) + (a + c.sRd * dL) / Dm;
+}
+
 template <bool kF64>
 __global__ void __launch_bounds__(256) check_kernel(const Consts c, int ngroups, int monotone,
                                                    PlanCheck *res) {
@@ -65,14 +85,16 @@ __global__ void __launch_bounds__(256) check_kernel(const Consts c, int ngroups,
     double prev64 = 0.0;
     long long prev = 0;
     for (int k = 0; k < c.K; ++k) {
-      const double t64 = depth_f64(gd, c.stp64[k], c) * scale;  // grid units
+      double t64;  // grid units
       long long t;
       if constexpr (kF64) {
+        t64 = depth_f64(gd, c.stp64[k], c) * scale;
         t = clamp32(t64);
         if (k > 0 && !(t64 > prev64) && bad == ~0ull && monotone)
           bad = ((unsigned long long)i << 32) | (unsigned)k;
       } else {
         t = depth_fx(c.grp[i], c.stp[k], c);
+        t64 = depth_f64_from(gd, c.stp64[k], c, (double)(int32_t)t, 1.0 / scale) * scale;
         ldev = max(ldev, clamp32(fabs((double)t - rint(t64))));
       }
       tlo = min(tlo, (int32_t)t);
