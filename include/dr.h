@@ -155,7 +155,11 @@ typedef struct {
  * beam, two centres at the same position along the beam) it uses the
  * interval kernel, which adds each interval by itself in any order; a
  * zero-length interval puts its difference in the bin that holds it.  The
- * wire must travel along the beam between its first and last centre
+ * interval kernel also takes scans that the running-sum kernels cannot
+ * (depth steps too fine for their fixed-point grid, tiles too large for
+ * shared memory), unless options give tile_cols or bin_groups: a launch
+ * shape that does not fit is then reported (DR_ERR_UNSUPPORTED).  The wire
+ * must travel along the beam between its first and last centre
  * (DR_ERR_GEOMETRY otherwise).
  *   wire_centres  host [K][3] FP64, K >= 2
  *   bin_edges     host [B+1] FP64 strictly increasing (depth, mm), B >= 1

@@ -140,11 +140,12 @@ def tuned_batch(jobs, reps=2, stream=None):
     import torch
 
     stream = stream or torch.cuda.current_stream()
-    best, timings = None, []
+    best, timings, refused = None, [], []
     for per_sm, cap, nt in BATCH_CANDIDATES:
         try:
             b = dr.Batch(jobs, ctas_per_sm=per_sm, max_tile_cols=cap, threads=nt)
-        except dr.DrError:
+        except dr.DrError as e:
+            refused.append(f"({per_sm}, {cap}, {nt}): {e}")
             continue
         b.launch(stream)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -163,6 +164,6 @@ def tuned_batch(jobs, reps=2, stream=None):
         else:
             b.close()
     if best is None:
-        raise RuntimeError("no batch configuration accepted")
+        raise RuntimeError("no batch configuration accepted: " + "; ".join(refused))
     return best[1], {"ctas_per_sm": best[2], "max_tile_cols": best[3], "threads": best[4],
                      "candidates": timings}

@@ -37,6 +37,9 @@ using namespace dr;
 namespace {
 
 constexpr int kBatchThreads = 512;
+// tiles per work item (consecutive rows, same columns): the work counter's
+// round trip and the scan lookup are paid once per item
+constexpr int kRowsPerItem = 2;
 
 void destroy(dr_batch_t *b) {
   if (!b) return;
@@ -85,11 +88,17 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
       return DR_ERR_INVALID_ARG;
     }
     const bool rows = p->kernel == DR_KERNEL_ROWS;
-    if (!p->parts.empty() || (!rows && p->kernel != DR_KERNEL_PIXELS) ||
-        p->geom_prec != DR_GEOM_FP32 || p->cols % 8 != 0 || (rows && p->tune.ppt != 4)) {
-      set_error("dr_batch_create: job %d: the batch runs single-run, single-edge plans of the "
-                "rows or per-pixel kernel with FP32 geometry on widths that are multiples of 8",
-                i);
+    const char *why = !p->parts.empty() ? "a composite plan (monotone runs or both edges)"
+                      : (!rows && p->kernel != DR_KERNEL_PIXELS) ? "an interval-kernel plan"
+                      : p->geom_prec != DR_GEOM_FP32              ? "FP64 geometry"
+                      : p->cols % 8 != 0                          ? "a width not a multiple of 8"
+                      : (rows && p->tune.ppt != 4)                ? "one pixel per thread"
+                                                                  : nullptr;
+    if (why) {
+      set_error("dr_batch_create: job %d is %s; the batch runs single-run, single-edge plans "
+                "of the rows or per-pixel kernel with FP32 geometry on widths that are "
+                "multiples of 8",
+                i, why);
       return DR_ERR_UNSUPPORTED;
     }
     if (out_dtype >= 0 && p->out_dtype != out_dtype) {
@@ -151,6 +160,7 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
     d.c = p->c;
     d.t = t;
     d.tiles_per_row = (p->cols + t.tile_cols - 1) / t.tile_cols;
+    d.rows_per_item = kRowsPerItem;
     if (rows)
       d.kind = kBatchRows;
     else if (p->c.depth_mode == kDepthPoly)
@@ -176,7 +186,8 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
   for (int i : order) {
     BatchScan d = desc[i];
     d.item_begin = items;
-    items += (long long)jobs[i].plan->rows * d.tiles_per_row;
+    items += (long long)((jobs[i].plan->rows + d.rows_per_item - 1) / d.rows_per_item) *
+             d.tiles_per_row;
     if (d.c.H * (long long)d.c.W == 0) continue;  // empty ROI: no items
     sorted.push_back(d);
   }

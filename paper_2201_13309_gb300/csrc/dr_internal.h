@@ -67,15 +67,16 @@ int rows_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64);
 int pixels_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64);
 // The per-pixel kernel of the polynomial form (no depth table).
 int pixels_poly_smem_bytes(int K, int Kpad, int B, int tile_cols);
-// Interval kernel: pixels per CTA (one warp each), and the shared-memory
-// bytes of one tile: mbarrier, image tile [Kpad][8] uint16, depths [K][8],
-// edges [B + 1], int64 accumulators [window][8] (dr_intervals.cuh).
+// Interval kernel: pixels per CTA, and the shared-memory bytes of one tile:
+// mbarrier, image tile [Kpad][8] uint16, depths [K][8], edges [B + 1], the
+// pixels' sums of |dI| (64 bytes), int32 accumulators [window][8]
+// (dr_intervals.cuh).
 constexpr int kIntervalTile = 8;
 inline int intervals_smem(int K, int Kpad, int B, int window, bool f64) {
   const size_t ps = f64 ? 8 : 4;
   auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
   return (int)(128 + a16((size_t)Kpad * kIntervalTile * 2) + a16((size_t)K * kIntervalTile * ps) +
-               a16((size_t)(B + 1) * ps) + (size_t)window * kIntervalTile * 8);
+               a16((size_t)(B + 1) * ps) + 64 + (size_t)window * kIntervalTile * 4);
 }
 // TMA chunking of K steps for a tile width (128-byte aligned destinations).
 void choose_chunks(int K, int tile_cols, int *kc, int *nchunks);

@@ -18,15 +18,22 @@
 // TMA as in the other kernels, depths of the 8 pixels in shared memory); a
 // warp covers 4 steps x the 8 pixels when it evaluates depths, and 4 chunks
 // of consecutive intervals x the 8 pixels when it apportions.  The bins go
-// through shared-memory windows of `window` int64 accumulators per pixel.
+// through shared-memory windows of `window` int32 accumulators per pixel.
 // Each thread splits its chunk into strictly monotone runs (and zero-length
-// intervals) and walks each run once over the bins it spans, adding
-// Phi(e_{j+1}) - Phi(e_j) summed over the run's intervals, Phi(e) =
-// round(dI * phi(e) * 2^30) on the fixed-point grid 2^-30 (so the parts of
-// one interval add up to dI exactly), with shared-memory atomics.  Integer
-// sums do not depend on the order of the atomics, so the result is
-// deterministic and does not depend on how the intervals are grouped.  The
-// window is then written out, 8 pixels of one bin being one 32-byte sector.
+// intervals) and walks each run once over the bins it spans.  Over one run
+// the sum of dI_k * phi_k at an edge e is s * G(e) with G(e) = V_0 - V(e):
+// V interpolates the run's image values linearly in depth (clamped at both
+// ends of the run), V_0 is the value at its shallowest point, and s = +1 when
+// the depths rise with the step, -1 when they fall.  G is the per-pixel
+// kernel's running sum F over that run, evaluated the same way in FP32; the
+// bin gets s * (G(e_{j+1}) - G(e_j)), rounded onto the pixel's fixed-point
+// grid and added with a shared-memory atomic.  The grid is 2^-q with q chosen
+// from the pixel's M = sum_k |dI_k|, so that M 2^q < 2^29: every partial sum
+// of a bin stays inside int32 (the parts added to all bins of a pixel come to
+// M in absolute value, up to FP32 rounding), and a part is rounded by at most
+// M 2^-30.  Integer sums do not depend on the order of the atomics, so the
+// result is deterministic.  The window is then written out, 8 pixels of one
+// bin being one 32-byte sector.
 #pragma once
 
 #include "dr_device.cuh"
@@ -34,52 +41,28 @@
 
 namespace dr {
 
-constexpr float kIvScale = 1073741824.f;  // 2^30: fixed-point grid of the sums
-
-// round(q * 2^30) for |q| < 2^31 without 64-bit conversions (those run on
-// the FP64 pipe): q = i + r with i = trunc(q) and r = q - i exact, and
-// r * 2^30 < 2^30 in magnitude
-__device__ __forceinline__ long long iv_fix(float q) {
-  const int i = __float2int_rz(q);
-  const int r = __float2int_rn(__fmul_rn(__fsub_rn(q, (float)i), kIvScale));
-  return (long long)i * (1ll << 30) + r;
-}
-// Phi(e) = round(dI * phi(e) * 2^30), phi(e) = clamp((e - lo) / (hi - lo), 0, 1);
-// edges at or beyond an end give 0 or dI * 2^30 exactly
-__device__ __forceinline__ long long iv_phi(int32_t e, int32_t lo, int32_t hi, float inv_len,
-                                            int dI) {
-  if (e <= lo) return 0;
-  if (e >= hi) return (long long)dI * (1ll << 30);
-  const float f = fminf(__fmul_rn(__uint2float_rn((uint32_t)e - (uint32_t)lo), inv_len), 1.f);
-  return iv_fix(__fmul_rn((float)dI, f));
-}
-__device__ __forceinline__ long long iv_phi(double e, double lo, double hi, double inv_len,
-                                            int dI) {
-  if (e <= lo) return 0;
-  if (e >= hi) return (long long)dI * (1ll << 30);
-  const double f = fmin((e - lo) * inv_len, 1.0);
-  return __double2ll_rn((double)dI * f * (double)kIvScale);
-}
+// 2^q as a float, -126 <= q <= 127
+__device__ __forceinline__ float iv_pow2(int q) { return __int_as_float((127 + q) << 23); }
+// the grid exponent q of a pixel whose sum of |dI| is M: M 2^q < 2^29
+__device__ __forceinline__ int iv_grid(uint32_t M) { return 29 - (32 - __clz(M)); }
+// 1 / (b - a) for a < b, and the position of e in [a, b] as a fraction (e
+// clamped to the interval by the caller: a <= e <= b)
 __device__ __forceinline__ float iv_inv_len(int32_t lo, int32_t hi) {
-  return __frcp_rn(__uint2float_rn((uint32_t)hi - (uint32_t)lo));
+  return rcp_approx(__uint2float_rn((uint32_t)hi - (uint32_t)lo));
 }
 __device__ __forceinline__ double iv_inv_len(double lo, double hi) { return 1.0 / (hi - lo); }
-// accumulator (units of 2^-30) to FP32: hi * 4 + lo * 2^-30 with one
-// rounding while |hi| < 2^24, i.e. for bin values below 2^26 counts (any
-// real scan); larger values (extreme counts of thousands of steps piled into
-// one bin) are within one ulp
-__device__ __forceinline__ float iv_value(long long a) {
-  const int hi = (int)(a >> 32);
-  const uint32_t lo = (uint32_t)a;
-  return __fmaf_rn(__uint2float_rn(lo), 1.f / kIvScale, __fmul_rn((float)hi, 4.f));
+__device__ __forceinline__ float iv_frac(int32_t e, int32_t lo, float inv) {
+  return fminf(__fmul_rn(__uint2float_rn((uint32_t)e - (uint32_t)lo), inv), 1.f);
+}
+__device__ __forceinline__ float iv_frac(double e, double lo, double inv) {
+  return (float)fmin((e - lo) * inv, 1.0);
 }
 
 template <class Geo, class OutT, bool kTma>
-__global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                        const uint16_t *__restrict__ img,
-                                                        OutT *__restrict__ out, const Consts c,
-                                                        const Tuning t, int pixel_groups,
-                                                        int window) {
+__global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks)
+    intervals_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *__restrict__ img,
+                     OutT *__restrict__ out, const Consts c, const Tuning t, int pixel_groups,
+                     int window) {
   using pos_t = typename Geo::pos_t;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -90,8 +73,9 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
   pos_t *spos = reinterpret_cast<pos_t *>(smem + 128 + align16((size_t)Kpad * TC * 2));
   pos_t *sedge = reinterpret_cast<pos_t *>(reinterpret_cast<unsigned char *>(spos) +
                                            align16((size_t)K * TC * sizeof(pos_t)));
-  unsigned long long *acc = reinterpret_cast<unsigned long long *>(
-      reinterpret_cast<unsigned char *>(sedge) + align16((size_t)(B + 1) * sizeof(pos_t)));
+  uint32_t *ssum = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(sedge) +
+                                                align16((size_t)(B + 1) * sizeof(pos_t)));
+  int32_t *acc = reinterpret_cast<int32_t *>(ssum + 16);
   const int row = blockIdx.y, c0 = blockIdx.x * TC;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int ncols = min(TC, c.W - c0);
@@ -104,20 +88,30 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
   // shared-memory accesses to the [step][pixel] arrays are contiguous
   const int warp = tid >> 5, lane = tid & 31, nwarps = NT >> 5;
   const int lc = lane & (TC - 1), s4 = warp * 4 + (lane >> 3), S = nwarps * 4;
-  {  // depths of the tile: steps s4, s4 + S, ... of pixel lc, two at a time
-    if (lc < ncols) {
-      const auto g = Geo::group(c, pixel_groups ? row * c.W + c0 + lc : row);
-      const auto *steps = Geo::steps(c);
-      for (int k = s4; k < K; k += 2 * S) {
-        const int k2 = min(k + S, K - 1);
-        pos_t d0, d1;
-        Geo::depth2(g, steps[k], steps[k2], c, d0, d1);
-        spos[DR_IDX(k * TC + lc, K * TC, c.err)] = d0;
-        if (k + S < K) spos[DR_IDX((k + S) * TC + lc, K * TC, c.err)] = d1;
+  // depths in column lcs of the [step][pixel] array: every pixel's own, or
+  // the row's in column 0 when the geometry is shared along the row
+  const int lcs = pixel_groups ? lc : 0;
+  {
+    const auto *steps = Geo::steps(c);
+    if (pixel_groups) {  // steps s4, s4 + S, ... of pixel lc, two at a time
+      if (lc < ncols) {
+        const auto g = Geo::group(c, row * c.W + c0 + lc);
+        for (int k = s4; k < K; k += 2 * S) {
+          const int k2 = min(k + S, K - 1);
+          pos_t d0, d1;
+          Geo::depth2(g, steps[k], steps[k2], c, d0, d1);
+          spos[DR_IDX(k * TC + lc, K * TC, c.err)] = d0;
+          if (k + S < K) spos[DR_IDX((k + S) * TC + lc, K * TC, c.err)] = d1;
+        }
       }
+    } else {  // the row's depths, one step per thread
+      const auto g = Geo::group(c, row);
+      for (int k = tid; k < K; k += NT)
+        spos[DR_IDX(k * TC, K * TC, c.err)] = Geo::depth(g, steps[k], c);
     }
   }
   for (int j = tid; j <= B; j += NT) sedge[DR_IDX(j, B + 1, c.err)] = Geo::edge(c, j);
+  if (tid < TC) ssum[tid] = 0u;
   __syncthreads();  // also makes the mbarrier initialisation visible
   if constexpr (kTma) {
     const bool late = !mbar_wait_bounded(bar, 0, c.err);
@@ -150,62 +144,77 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
     return lo;
   };
 
-  // dI of interval m (the step pair it joins, in the plan's travel order)
-  auto step_dI = [&](int m) {
-    const int ia = rev ? K - 1 - m : m, ib = rev ? K - 2 - m : m + 1;
-    const int n_simg = Kpad * TC;
-    return (int)simg[DR_IDX(ia * TC + lc, n_simg, c.err)] -
-           (int)simg[DR_IDX(ib * TC + lc, n_simg, c.err)];
+  // image value (biased float) of step m in the plan's travel order, and
+  // dI of interval m (the step pair m, m + 1)
+  auto step_V = [&](int m) {
+    return biased(simg[DR_IDX((rev ? K - 1 - m : m) * TC + lc, Kpad * TC, c.err)]);
   };
+  auto step_dI = [&](int m) { return (int)__fsub_rn(step_V(m), step_V(m + 1)); };
+  {  // M = sum_k |dI_k| of each pixel: steps s4, s4 + S, ..., then the 4
+     // lanes of a warp that share the pixel, then the warps (atomics)
+    uint32_t part = 0u;
+    if (lc < ncols)
+      for (int k = s4; k < K - 1; k += S) part += (uint32_t)abs(step_dI(k));
+    part += __shfl_xor_sync(0xffffffffu, part, 8);
+    part += __shfl_xor_sync(0xffffffffu, part, 16);
+    if (lane < TC && part) atomicAdd(&ssum[lc], part);
+  }
   // intervals per chunk: one chunk per thread where K allows; odd, so that
   // the 4 chunks of a warp start in different banks
   const int C = ((K - 1 + S - 1) / S) | 1;
 
+  float q_scale = 0.f;  // 2^q of pixel lc, read once the sums are complete
   for (int wb0 = 0; wb0 < B; wb0 += window) {
     const int wb1 = min(wb0 + window, B);
-    const int nwin = (wb1 - wb0) * TC;  // even: 8 accumulators per bin
-    for (int i = tid; i < nwin / 2; i += NT)
-      reinterpret_cast<ulonglong2 *>(acc)[DR_IDX(i, window * TC / 2, c.err)] =
-          make_ulonglong2(0ull, 0ull);
-    __syncthreads();
+    const int nwin = (wb1 - wb0) * TC;  // 8 accumulators per bin
+    for (int i = tid; i < nwin / 4; i += NT)
+      reinterpret_cast<int4 *>(acc)[DR_IDX(i, window * TC / 4, c.err)] = make_int4(0, 0, 0, 0);
+    __syncthreads();  // (first window: also the pixels' sums of |dI|)
+    if (wb0 == 0) q_scale = iv_pow2(iv_grid(ssum[lc]));
     const pos_t ewlo = sedge[wb0], ewhi = sedge[wb1];
     // One strictly monotone run, intervals m .. n - 1, rising (up) or
-    // falling.  Taken in increasing depth, its positions are D(0) < ... <
-    // D(len) and interval i joins D(i) and D(i + 1).  At an edge e the sum
-    // over the run's intervals of Phi_k(e) is P(e) = (sum of dI * 2^30 over
-    // the intervals below e) + Phi of the interval holding e, so a bin gets
-    // P(e_{j+1}) - P(e_j): the same integer as the sum of the intervals'
-    // own differences, with one atomic per bin instead of one per interval.
+    // falling.  Taken in increasing depth, its points are D(0) < ... <
+    // D(len) (step m + i, or n - i when falling) with image values V(i);
+    // G(e) = V(0) - V(e), V interpolated in depth and clamped to the run, is
+    // formed as base + f * d with base = V(0) - V(i) and d = V(i) - V(i+1)
+    // on the interval [D(i), D(i+1)] that holds e, as the per-pixel walk
+    // forms its running sum.
     auto iv_run = [&](int m, int n, bool up) {
+      auto step_of = [&](int i) { return up ? m + i : n - i; };
+      auto D = [&](int i) { return spos[DR_IDX(step_of(i) * TC + lcs, K * TC, c.err)]; };
       const int len = n - m;
-      auto D = [&](int i) { return spos[DR_IDX((up ? m + i : n - i) * TC + lc, K * TC, c.err)]; };
       const pos_t lo_run = D(0), hi_run = D(len);
       if (lo_run >= ewhi || hi_run < ewlo) return;  // nothing in this window
       int i = 0;
-      pos_t lo_i = lo_run, hi_i = D(1);
-      int dI = step_dI(up ? m : n - 1);
-      auto inv = iv_inv_len(lo_i, hi_i);
-      long long cum = 0;  // dI * 2^30 summed over the intervals below i
-      auto P = [&](pos_t e) {
-        while (i < len && !(e < hi_i)) {
-          cum += (long long)dI * (1ll << 30);
-          if (++i < len) {
-            lo_i = hi_i;
-            hi_i = D(i + 1);
-            dI = step_dI(up ? m + i : n - 1 - i);
-            inv = iv_inv_len(lo_i, hi_i);
-          }
+      pos_t t0 = lo_run, t1 = D(1);
+      const float V0 = step_V(step_of(0));
+      float V1 = step_V(step_of(1));
+      float base = 0.f, d = __fsub_rn(V0, V1);
+      auto inv = iv_inv_len(t0, t1);
+      auto G = [&](pos_t e) {
+        const pos_t ec = e < hi_run ? e : hi_run;
+        while (t1 < ec) {  // stops at the last point: t1 = D(len) >= ec
+          ++i;
+          t0 = t1;
+          t1 = D(i + 1);
+          const float Vn = step_V(step_of(i + 1));
+          base = __fsub_rn(V0, V1);
+          d = __fsub_rn(V1, Vn);
+          V1 = Vn;
+          inv = iv_inv_len(t0, t1);
         }
-        return i < len ? cum + iv_phi(e, lo_i, hi_i, inv, dI) : cum;
+        return __fmaf_rn(iv_frac(ec > t0 ? ec : t0, t0, inv), d, base);
       };
+      const float sg = up ? 1.f : -1.f;
       int j = max(count_le(lo_run) - 1, wb0);
-      long long p0 = P(sedge[DR_IDX(j, B + 1, c.err)]);
+      float g0 = G(sedge[DR_IDX(j, B + 1, c.err)]);
       for (; j < wb1 && sedge[DR_IDX(j, B + 1, c.err)] < hi_run; ++j) {
-        const long long p1 = P(sedge[DR_IDX(j + 1, B + 1, c.err)]);
-        if (p1 != p0)
+        const float g1 = G(sedge[DR_IDX(j + 1, B + 1, c.err)]);
+        const float v = __fmul_rn(sg, __fsub_rn(g1, g0));
+        if (v != 0.f)
           atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
-                    (unsigned long long)(p1 - p0));
-        p0 = p1;
+                    __float2int_rn(__fmul_rn(v, q_scale)));
+        g0 = g1;
       }
     };
     // chunks of C consecutive intervals of pixel lc, chunk q = s4, s4 + S,
@@ -214,21 +223,21 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
     for (int q = s4; q * C < K - 1 && lc < ncols; q += S) {
       const int m1 = min(q * C + C, K - 1);
       for (int m = q * C; m < m1;) {
-        const pos_t a = spos[DR_IDX(m * TC + lc, K * TC, c.err)],
-                    b = spos[DR_IDX((m + 1) * TC + lc, K * TC, c.err)];
+        const pos_t a = spos[DR_IDX(m * TC + lcs, K * TC, c.err)],
+                    b = spos[DR_IDX((m + 1) * TC + lcs, K * TC, c.err)];
         if (!(a < b) && !(b < a)) {  // zero length: the bin [e_j, e_{j+1}) holding a
           const int dI = step_dI(m);
           const int j = count_le(a) - 1;
           if (dI != 0 && j >= wb0 && j < wb1)
             atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
-                      (unsigned long long)((long long)dI * (1ll << 30)));
+                      __float2int_rn(__fmul_rn((float)dI, q_scale)));
           ++m;
           continue;
         }
         const bool up = a < b;
         int n = m + 1;  // the run: intervals m .. n - 1
         for (pos_t prev = b; n < m1; ++n) {
-          const pos_t nx = spos[DR_IDX((n + 1) * TC + lc, K * TC, c.err)];
+          const pos_t nx = spos[DR_IDX((n + 1) * TC + lcs, K * TC, c.err)];
           if (up ? !(prev < nx) : !(nx < prev)) break;
           prev = nx;
         }
@@ -239,19 +248,20 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
     __syncthreads();
     if (!acc_out && ncols == TC && c.W % 4 == 0 &&
         ((uintptr_t)out & (4 * sizeof(OutT) - 1)) == 0) {
-      // 4 pixels per thread: two 16-byte shared loads, one vector store
+      // 4 pixels per thread (the same 4 in every pass: NT is even): one
+      // 16-byte shared load, one vector store
+      const int half = tid & 1;
+      float w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        w[u] = __fmul_rn(sign, iv_pow2(-iv_grid(ssum[4 * half + u])));
       for (int q = tid; q < nwin / 4; q += NT) {
-        const int jj = q >> 1, half = q & 1;
-        const ulonglong2 a =
-            reinterpret_cast<const ulonglong2 *>(acc)[DR_IDX(2 * q, window * TC / 2, c.err)];
-        const ulonglong2 b =
-            reinterpret_cast<const ulonglong2 *>(acc)[DR_IDX(2 * q + 1, window * TC / 2, c.err)];
-        OutT *o = DR_PTR(out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + 4 * half,
+        const int4 a = reinterpret_cast<const int4 *>(acc)[DR_IDX(q, window * TC / 4, c.err)];
+        OutT *o = DR_PTR(out + (size_t)(wb0 + (q >> 1)) * plane + (size_t)row * c.W + c0 +
+                             4 * half,
                          out, plane * B - 3, c.err);
-        st_cs4(o, __fmul_rn(sign, iv_value((long long)a.x)),
-               __fmul_rn(sign, iv_value((long long)a.y)),
-               __fmul_rn(sign, iv_value((long long)b.x)),
-               __fmul_rn(sign, iv_value((long long)b.y)));
+        st_cs4(o, __fmul_rn(__int2float_rn(a.x), w[0]), __fmul_rn(__int2float_rn(a.y), w[1]),
+               __fmul_rn(__int2float_rn(a.z), w[2]), __fmul_rn(__int2float_rn(a.w), w[3]));
       }
     } else {
       for (int i = tid; i < nwin; i += NT) {
@@ -259,11 +269,12 @@ __global__ void __launch_bounds__(512) intervals_kernel(const __grid_constant__ 
         if (px >= ncols) continue;
         OutT *o = DR_PTR(out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + px, out,
                          plane * B, c.err);
-        const float v = __fmul_rn(sign, iv_value((long long)acc[DR_IDX(i, window * TC, c.err)]));
+        const float v = __fmul_rn(__int2float_rn(acc[DR_IDX(i, window * TC, c.err)]),
+                                  __fmul_rn(sign, iv_pow2(-iv_grid(ssum[px]))));
         st_cs(o, acc_out ? __fadd_rn(out_load(o), v) : v);
       }
     }
-    __syncthreads();  // the window's accumulators are reused
+    if (wb1 < B) __syncthreads();  // the window's accumulators are reused
   }
 }
 

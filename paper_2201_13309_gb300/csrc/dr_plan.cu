@@ -509,8 +509,8 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
                               : pixels_smem_bytes(K, kc * n, B, tc, f64);
   };
   if (intervals) {
-    // 8 pixels x all steps per CTA, one warp per pixel; bins in windows of
-    // int64 accumulators sized for two CTAs per SM (one if that is too small)
+    // 8 pixels x all steps per CTA; bins in windows of int32 accumulators,
+    // all bins in one window for three or two CTAs per SM where they fit
     t.ppt = 1;
     t.tile_cols = kIntervalTile;
     t.bin_groups = 1;
@@ -581,9 +581,11 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   }
   if (intervals) {
     const size_t fixed = (size_t)intervals_smem(K, t.kc * t.nchunks, B, 0, f64);
-    size_t budget = (size_t)(kSmemPerSm / 2 - 1024);
-    if (fixed + 32 * 64 > budget) budget = (size_t)kSmemPerCtaMax;
-    const long long win = fixed < budget ? (long long)((budget - fixed) / 64) : 0;
+    const size_t per_bin = (size_t)kIntervalTile * 4;
+    size_t budget = (size_t)(kSmemPerSm / 3 - 1024);
+    if (fixed + per_bin * B > budget) budget = (size_t)(kSmemPerSm / 2 - 1024);
+    if (fixed + per_bin * 32 > budget) budget = (size_t)kSmemPerCtaMax;
+    const long long win = fixed < budget ? (long long)((budget - fixed) / per_bin) : 0;
     if (win < std::min(B, 32)) {
       delete p;
       set_error("dr_plan: %d steps x %d bins do not fit the interval kernel's shared memory", K,
@@ -923,10 +925,14 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t 
   dr_status st = plan_parts(false, g, wires, K, edges, B, opt, starts, travel, out);
   if (st == DR_ERR_NONMONOTONIC)  // depth runs against its wire run somewhere
     return plan_parts(true, g, wires, K, edges, B, opt, one, travel, out);
-  if (st == DR_ERR_UNSUPPORTED && !(opt && opt->force_pixels)) {
+  const bool shape_given = opt && (opt->tile_cols || opt->bin_groups);
+  if (st == DR_ERR_UNSUPPORTED && !(opt && opt->force_pixels) && !shape_given) {
     // outside what the running-sum kernels take (depth steps too fine for
     // their fixed-point grid, tile memory): the interval kernel needs neither;
-    // if it cannot take the scan either, the first reason is reported
+    // if it cannot take the scan either, the first reason is reported.  A
+    // launch shape given by the caller is for the running-sum kernels, so a
+    // shape that does not fit is reported rather than replaced by the
+    // interval kernel.
     char first[sizeof(g_msg)];
     std::memcpy(first, g_msg, sizeof(g_msg));
     if (plan_parts(true, g, wires, K, edges, B, opt, one, travel, out) == DR_OK) return DR_OK;
