@@ -137,3 +137,20 @@ def test_climbing_wire_takes_the_exact_form():
     sc.wires = synth.wire_path(25, dy=0.0002)
     plan = dr.Plan(sc.geom, sc.wires, sc.edges)
     assert plan.info()["depth_form"] == 0
+
+
+def test_launch_shape_that_does_not_fit_is_reported():
+    """A tile width given by the caller is a request for the running-sum
+    kernels: when its tile does not fit in shared memory (801 steps x 256
+    columns of images), dr_plan reports it instead of handing the scan to
+    the interval kernel; without a given shape the plan picks a tile that
+    fits."""
+    geom = synth.detector_geometry(8, 256)
+    wires = synth.wire_path(801)
+    edges = synth.bin_edges(-400.0, 400.0, 1.0)
+    with pytest.raises(dr.DrError) as e:
+        dr.Plan(geom, wires, edges, tile_cols=256, bin_groups=2)
+    assert e.value.status == 8  # DR_ERR_UNSUPPORTED
+    plan = dr.Plan(geom, wires, edges)
+    assert plan.info()["kernel"] == "rows"
+    plan.close()
