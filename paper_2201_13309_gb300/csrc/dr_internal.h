@@ -68,15 +68,16 @@ int pixels_smem_bytes(int K, int Kpad, int B, int tile_cols, bool f64);
 // The per-pixel kernel of the polynomial form (no depth table).
 int pixels_poly_smem_bytes(int K, int Kpad, int B, int tile_cols);
 // Interval kernel: pixels per CTA, and the shared-memory bytes of one tile:
-// mbarrier, image tile [Kpad][8] uint16, depths [K][8], edges [B + 1], the
-// pixels' sums of |dI| (64 bytes), int32 accumulators [window][8]
-// (dr_intervals.cuh).
-constexpr int kIntervalTile = 8;
-inline int intervals_smem(int K, int Kpad, int B, int window, bool f64) {
-  const size_t ps = f64 ? 8 : 4;
+// mbarrier, image tile [Kpad][32] uint16, depths [K][32] (per-pixel
+// geometry) or [K] (shared along the row), edges [B + 1], the pixels' sums of
+// |dI| (128 bytes), int32 accumulators [window][32] (dr_intervals.cuh).
+constexpr int kIntervalTile = 32;
+inline int intervals_smem(int K, int Kpad, int B, int window, bool f64, bool per_pixel) {
+  const size_t ps = f64 ? 8 : 4, cols = per_pixel ? kIntervalTile : 1;
   auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
-  return (int)(128 + a16((size_t)Kpad * kIntervalTile * 2) + a16((size_t)K * kIntervalTile * ps) +
-               a16((size_t)(B + 1) * ps) + 64 + (size_t)window * kIntervalTile * 4);
+  return (int)(128 + a16((size_t)Kpad * kIntervalTile * 2) + a16((size_t)K * cols * ps) +
+               a16((size_t)(B + 1) * ps) + 4 * kIntervalTile +
+               (size_t)window * kIntervalTile * 4);
 }
 // TMA chunking of K steps for a tile width (128-byte aligned destinations).
 void choose_chunks(int K, int tile_cols, int *kc, int *nchunks);

@@ -14,11 +14,13 @@
 // and an interval of zero length puts its whole dI_k into the bin
 // [e_j, e_{j+1}) that holds it.  Mass outside [e_0, e_B] is dropped.
 //
-// A CTA owns one row x 8 adjacent pixels x all K steps (image tile staged by
-// TMA as in the other kernels, depths of the 8 pixels in shared memory); a
-// warp covers 4 steps x the 8 pixels when it evaluates depths, and 4 chunks
-// of consecutive intervals x the 8 pixels when it apportions.  The bins go
-// through shared-memory windows of `window` int32 accumulators per pixel.
+// A CTA owns one row x 32 adjacent pixels x all K steps (image tile staged by
+// TMA as in the other kernels; the depths in shared memory, per pixel, or
+// once for the row when the geometry is shared along it).  Lane = pixel and
+// warp = a chunk of consecutive intervals, so every shared-memory access of a
+// warp touches 32 consecutive words, and one bin of the tile is a 128-byte
+// line of its output plane.  The bins go through shared-memory windows of
+// `window` int32 accumulators per pixel.
 // Each thread splits its chunk into strictly monotone runs (and zero-length
 // intervals) and walks each run once over the bins it spans.  Over one run
 // the sum of dI_k * phi_k at an edge e is s * G(e) with G(e) = V_0 - V(e):
@@ -32,8 +34,7 @@
 // of a bin stays inside int32 (the parts added to all bins of a pixel come to
 // M in absolute value, up to FP32 rounding), and a part is rounded by at most
 // M 2^-30.  Integer sums do not depend on the order of the atomics, so the
-// result is deterministic.  The window is then written out, 8 pixels of one
-// bin being one 32-byte sector.
+// result is deterministic.
 #pragma once
 
 #include "dr_device.cuh"
@@ -58,56 +59,58 @@ __device__ __forceinline__ float iv_frac(double e, double lo, double inv) {
   return (float)fmin((e - lo) * inv, 1.0);
 }
 
+// Shared-memory layout (intervals_smem): [0, 128) mbarrier, the image tile
+// [Kpad][32] uint16, the depths [K][32] (pixel_groups) or [K], the edges
+// [B + 1], the pixels' sums of |dI| [32], the accumulators [window][32].
+// (two CTAs per SM with FP32 geometry, one with FP64)
 template <class Geo, class OutT, bool kTma>
-__global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks)
+__global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
     intervals_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *__restrict__ img,
                      OutT *__restrict__ out, const Consts c, const Tuning t, int pixel_groups,
                      int window) {
   using pos_t = typename Geo::pos_t;
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-  uint16_t *simg = reinterpret_cast<uint16_t *>(smem + 128);
   constexpr int TC = kIntervalTile;
+  extern __shared__ __align__(128) unsigned char smem[];
   const int K = c.K, B = c.B;
   const int Kpad = t.kc * t.nchunks;
+  const int PS = pixel_groups ? TC : 1;  // depth columns
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  uint16_t *simg = reinterpret_cast<uint16_t *>(smem + 128);
   pos_t *spos = reinterpret_cast<pos_t *>(smem + 128 + align16((size_t)Kpad * TC * 2));
   pos_t *sedge = reinterpret_cast<pos_t *>(reinterpret_cast<unsigned char *>(spos) +
-                                           align16((size_t)K * TC * sizeof(pos_t)));
+                                           align16((size_t)K * PS * sizeof(pos_t)));
   uint32_t *ssum = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(sedge) +
                                                 align16((size_t)(B + 1) * sizeof(pos_t)));
-  int32_t *acc = reinterpret_cast<int32_t *>(ssum + 16);
+  int32_t *acc = reinterpret_cast<int32_t *>(ssum + TC);
   const int row = blockIdx.y, c0 = blockIdx.x * TC;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int ncols = min(TC, c.W - c0);
+  // thread = (pixel lc, chunk slot warp); with 32 pixels a slot is a warp
+  const int lc = tid & (TC - 1), warp = tid / TC, nw = NT / TC;
+  const int lcs = pixel_groups ? lc : 0;  // this pixel's depth column
+  const bool valid = lc < ncols;
 
   if constexpr (kTma) {
     if (tid == 0) mbar_init(bar, 1);
   }
   stage_tile<kTma>(&tmap, img, simg, bar, c, t, row, c0);
-  // a warp covers 4 steps x the 8 pixels (lane = 8 * step + pixel), so its
-  // shared-memory accesses to the [step][pixel] arrays are contiguous
-  const int warp = tid >> 5, lane = tid & 31, nwarps = NT >> 5;
-  const int lc = lane & (TC - 1), s4 = warp * 4 + (lane >> 3), S = nwarps * 4;
-  // depths in column lcs of the [step][pixel] array: every pixel's own, or
-  // the row's in column 0 when the geometry is shared along the row
-  const int lcs = pixel_groups ? lc : 0;
   {
     const auto *steps = Geo::steps(c);
-    if (pixel_groups) {  // steps s4, s4 + S, ... of pixel lc, two at a time
-      if (lc < ncols) {
+    if (pixel_groups) {  // steps warp, warp + nw, ... of pixel lc, two at a time
+      if (valid) {
         const auto g = Geo::group(c, row * c.W + c0 + lc);
-        for (int k = s4; k < K; k += 2 * S) {
-          const int k2 = min(k + S, K - 1);
+        for (int k = warp; k < K; k += 2 * nw) {
+          const int k2 = min(k + nw, K - 1);
           pos_t d0, d1;
           Geo::depth2(g, steps[k], steps[k2], c, d0, d1);
-          spos[DR_IDX(k * TC + lc, K * TC, c.err)] = d0;
-          if (k + S < K) spos[DR_IDX((k + S) * TC + lc, K * TC, c.err)] = d1;
+          spos[DR_IDX(k * TC + lc, K * PS, c.err)] = d0;
+          if (k + nw < K) spos[DR_IDX((k + nw) * TC + lc, K * PS, c.err)] = d1;
         }
       }
     } else {  // the row's depths, one step per thread
       const auto g = Geo::group(c, row);
       for (int k = tid; k < K; k += NT)
-        spos[DR_IDX(k * TC, K * TC, c.err)] = Geo::depth(g, steps[k], c);
+        spos[DR_IDX(k, K * PS, c.err)] = Geo::depth(g, steps[k], c);
     }
   }
   for (int j = tid; j <= B; j += NT) sedge[DR_IDX(j, B + 1, c.err)] = Geo::edge(c, j);
@@ -122,6 +125,33 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks)
   const float sign = c.out_sign;
   const size_t plane = (size_t)c.H * c.W;
   const bool acc_out = c.accumulate != 0;
+  // image value (biased float) of step m in the plan's travel order, and
+  // dI of interval m (the step pair m, m + 1)
+  auto step_V = [&](int m) {
+    return biased(simg[DR_IDX((rev ? K - 1 - m : m) * TC + lc, Kpad * TC, c.err)]);
+  };
+  auto step_dI = [&](int m) { return (int)__fsub_rn(step_V(m), step_V(m + 1)); };
+  // this thread's chunk of consecutive intervals m0 .. m1 - 1 of pixel lc
+  // (one chunk per slot: C * nw >= K - 1), its range of depths, and M =
+  // sum_k |dI_k| of each pixel (the chunks' sums, one atomic per chunk)
+  const int C = (K - 1 + nw - 1) / nw;
+  const int m0 = warp * C, m1 = min(m0 + C, K - 1);
+  const bool has_chunk = valid && m0 < m1;
+  pos_t cmin = 0, cmax = 0;
+  if (has_chunk) {
+    uint32_t part = 0u;
+    float Vp = step_V(m0);
+    cmin = cmax = spos[DR_IDX(m0 * PS + lcs, K * PS, c.err)];
+    for (int m = m0; m < m1; ++m) {
+      const float Vn = step_V(m + 1);
+      part += (uint32_t)abs((int)__fsub_rn(Vp, Vn));
+      Vp = Vn;
+      const pos_t d = spos[DR_IDX((m + 1) * PS + lcs, K * PS, c.err)];
+      cmin = d < cmin ? d : cmin;
+      cmax = d > cmax ? d : cmax;
+    }
+    if (part) atomicAdd(&ssum[lc], part);
+  }
   // number of edges e_i <= x (0..B+1): a guess from the mean bin width,
   // checked against its two neighbouring edges and moved by up to two edges;
   // a binary search when that does not settle it (uneven bins)
@@ -144,29 +174,10 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks)
     return lo;
   };
 
-  // image value (biased float) of step m in the plan's travel order, and
-  // dI of interval m (the step pair m, m + 1)
-  auto step_V = [&](int m) {
-    return biased(simg[DR_IDX((rev ? K - 1 - m : m) * TC + lc, Kpad * TC, c.err)]);
-  };
-  auto step_dI = [&](int m) { return (int)__fsub_rn(step_V(m), step_V(m + 1)); };
-  {  // M = sum_k |dI_k| of each pixel: steps s4, s4 + S, ..., then the 4
-     // lanes of a warp that share the pixel, then the warps (atomics)
-    uint32_t part = 0u;
-    if (lc < ncols)
-      for (int k = s4; k < K - 1; k += S) part += (uint32_t)abs(step_dI(k));
-    part += __shfl_xor_sync(0xffffffffu, part, 8);
-    part += __shfl_xor_sync(0xffffffffu, part, 16);
-    if (lane < TC && part) atomicAdd(&ssum[lc], part);
-  }
-  // intervals per chunk: one chunk per thread where K allows; odd, so that
-  // the 4 chunks of a warp start in different banks
-  const int C = ((K - 1 + S - 1) / S) | 1;
-
   float q_scale = 0.f;  // 2^q of pixel lc, read once the sums are complete
   for (int wb0 = 0; wb0 < B; wb0 += window) {
     const int wb1 = min(wb0 + window, B);
-    const int nwin = (wb1 - wb0) * TC;  // 8 accumulators per bin
+    const int nwin = (wb1 - wb0) * TC;  // 32 accumulators per bin
     for (int i = tid; i < nwin / 4; i += NT)
       reinterpret_cast<int4 *>(acc)[DR_IDX(i, window * TC / 4, c.err)] = make_int4(0, 0, 0, 0);
     __syncthreads();  // (first window: also the pixels' sums of |dI|)
@@ -180,24 +191,30 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks)
     // on the interval [D(i), D(i+1)] that holds e, as the per-pixel walk
     // forms its running sum.
     auto iv_run = [&](int m, int n, bool up) {
-      auto step_of = [&](int i) { return up ? m + i : n - i; };
-      auto D = [&](int i) { return spos[DR_IDX(step_of(i) * TC + lcs, K * TC, c.err)]; };
-      const int len = n - m;
-      const pos_t lo_run = D(0), hi_run = D(len);
+      // the run's points in increasing depth: positions at pd (stride ds)
+      // and image values at pv (stride vs), starting at D(0)
+      const int len = n - m, s0 = up ? m : n;
+      const int ds = up ? PS : -PS, vs = (up != rev) ? TC : -TC;
+      const pos_t *pd = spos + s0 * PS + lcs;
+      const uint16_t *pv = simg + (rev ? K - 1 - s0 : s0) * TC + lc;
+      const pos_t lo_run = *DR_PTR(pd, spos, K * PS, c.err);
+      const pos_t hi_run = *DR_PTR(pd + len * ds, spos, K * PS, c.err);
       if (lo_run >= ewhi || hi_run < ewlo) return;  // nothing in this window
-      int i = 0;
-      pos_t t0 = lo_run, t1 = D(1);
-      const float V0 = step_V(step_of(0));
-      float V1 = step_V(step_of(1));
+      pd += ds;
+      pos_t t0 = lo_run, t1 = *DR_PTR(pd, spos, K * PS, c.err);
+      const float V0 = biased(*DR_PTR(pv, simg, Kpad * TC, c.err));
+      pv += vs;
+      float V1 = biased(*DR_PTR(pv, simg, Kpad * TC, c.err));
       float base = 0.f, d = __fsub_rn(V0, V1);
       auto inv = iv_inv_len(t0, t1);
       auto G = [&](pos_t e) {
         const pos_t ec = e < hi_run ? e : hi_run;
         while (t1 < ec) {  // stops at the last point: t1 = D(len) >= ec
-          ++i;
           t0 = t1;
-          t1 = D(i + 1);
-          const float Vn = step_V(step_of(i + 1));
+          pd += ds;
+          t1 = *DR_PTR(pd, spos, K * PS, c.err);
+          pv += vs;
+          const float Vn = biased(*DR_PTR(pv, simg, Kpad * TC, c.err));
           base = __fsub_rn(V0, V1);
           d = __fsub_rn(V1, Vn);
           V1 = Vn;
@@ -205,26 +222,27 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks)
         }
         return __fmaf_rn(iv_frac(ec > t0 ? ec : t0, t0, inv), d, base);
       };
-      const float sg = up ? 1.f : -1.f;
-      int j = max(count_le(lo_run) - 1, wb0);
-      float g0 = G(sedge[DR_IDX(j, B + 1, c.err)]);
-      for (; j < wb1 && sedge[DR_IDX(j, B + 1, c.err)] < hi_run; ++j) {
-        const float g1 = G(sedge[DR_IDX(j + 1, B + 1, c.err)]);
-        const float v = __fmul_rn(sg, __fsub_rn(g1, g0));
+      const float scale = up ? q_scale : -q_scale;  // the run's sign and the pixel's grid
+      const int j0 = max(count_le(lo_run) - 1, wb0);
+      const pos_t *pe = sedge + j0;
+      int32_t *pa = acc + (j0 - wb0) * TC + lc;
+      int32_t *const pa_end = acc + (wb1 - wb0) * TC;
+      float g0 = G(*DR_PTR(pe, sedge, B + 1, c.err));
+      for (; pa < pa_end && *DR_PTR(pe, sedge, B + 1, c.err) < hi_run; ++pe, pa += TC) {
+        const float g1 = G(*DR_PTR(pe + 1, sedge, B + 1, c.err));
+        const float v = __fsub_rn(g1, g0);
         if (v != 0.f)
-          atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
-                    __float2int_rn(__fmul_rn(v, q_scale)));
+          atomicAdd(DR_PTR(pa, acc, window * TC, c.err), __float2int_rn(__fmul_rn(v, scale)));
         g0 = g1;
       }
     };
-    // chunks of C consecutive intervals of pixel lc, chunk q = s4, s4 + S,
-    // ...; a chunk splits into strictly monotone runs and zero-length
-    // intervals, and each run is walked once over the bins it spans
-    for (int q = s4; q * C < K - 1 && lc < ncols; q += S) {
-      const int m1 = min(q * C + C, K - 1);
-      for (int m = q * C; m < m1;) {
-        const pos_t a = spos[DR_IDX(m * TC + lcs, K * TC, c.err)],
-                    b = spos[DR_IDX((m + 1) * TC + lcs, K * TC, c.err)];
+    // the chunk splits into strictly monotone runs and zero-length
+    // intervals, and each run is walked once over the bins it spans; a chunk
+    // whose depths miss the window is skipped whole
+    if (has_chunk && cmax >= ewlo && cmin < ewhi) {
+      for (int m = m0; m < m1;) {
+        const pos_t a = spos[DR_IDX(m * PS + lcs, K * PS, c.err)],
+                    b = spos[DR_IDX((m + 1) * PS + lcs, K * PS, c.err)];
         if (!(a < b) && !(b < a)) {  // zero length: the bin [e_j, e_{j+1}) holding a
           const int dI = step_dI(m);
           const int j = count_le(a) - 1;
@@ -237,7 +255,7 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks)
         const bool up = a < b;
         int n = m + 1;  // the run: intervals m .. n - 1
         for (pos_t prev = b; n < m1; ++n) {
-          const pos_t nx = spos[DR_IDX((n + 1) * TC + lcs, K * TC, c.err)];
+          const pos_t nx = spos[DR_IDX((n + 1) * PS + lcs, K * PS, c.err)];
           if (up ? !(prev < nx) : !(nx < prev)) break;
           prev = nx;
         }
@@ -248,29 +266,27 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks)
     __syncthreads();
     if (!acc_out && ncols == TC && c.W % 4 == 0 &&
         ((uintptr_t)out & (4 * sizeof(OutT) - 1)) == 0) {
-      // 4 pixels per thread (the same 4 in every pass: NT is even): one
-      // 16-byte shared load, one vector store
-      const int half = tid & 1;
+      // 4 pixels per thread (the same 4 in every pass: NT is a multiple of
+      // TC / 4), one 16-byte shared load and one vector store; TC / 4 threads
+      // store a bin's line of 4 TC bytes
+      const int p0 = (tid % (TC / 4)) * 4;
       float w[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        w[u] = __fmul_rn(sign, iv_pow2(-iv_grid(ssum[4 * half + u])));
+      for (int u = 0; u < 4; ++u) w[u] = __fmul_rn(sign, iv_pow2(-iv_grid(ssum[p0 + u])));
       for (int q = tid; q < nwin / 4; q += NT) {
         const int4 a = reinterpret_cast<const int4 *>(acc)[DR_IDX(q, window * TC / 4, c.err)];
-        OutT *o = DR_PTR(out + (size_t)(wb0 + (q >> 1)) * plane + (size_t)row * c.W + c0 +
-                             4 * half,
+        OutT *o = DR_PTR(out + (size_t)(wb0 + q / (TC / 4)) * plane + (size_t)row * c.W + c0 + p0,
                          out, plane * B - 3, c.err);
         st_cs4(o, __fmul_rn(__int2float_rn(a.x), w[0]), __fmul_rn(__int2float_rn(a.y), w[1]),
                __fmul_rn(__int2float_rn(a.z), w[2]), __fmul_rn(__int2float_rn(a.w), w[3]));
       }
     } else {
-      for (int i = tid; i < nwin; i += NT) {
-        const int jj = i / TC, px = i - jj * TC;
-        if (px >= ncols) continue;
-        OutT *o = DR_PTR(out + (size_t)(wb0 + jj) * plane + (size_t)row * c.W + c0 + px, out,
-                         plane * B, c.err);
-        const float v = __fmul_rn(__int2float_rn(acc[DR_IDX(i, window * TC, c.err)]),
-                                  __fmul_rn(sign, iv_pow2(-iv_grid(ssum[px]))));
+      const float w = __fmul_rn(sign, iv_pow2(-iv_grid(ssum[lc])));
+      for (int i = tid; i < nwin; i += NT) {  // i % TC = lc: NT is a multiple of TC
+        if (!valid) continue;
+        OutT *o = DR_PTR(out + (size_t)(wb0 + i / TC) * plane + (size_t)row * c.W + c0 + lc,
+                         out, plane * B, c.err);
+        const float v = __fmul_rn(__int2float_rn(acc[DR_IDX(i, window * TC, c.err)]), w);
         st_cs(o, acc_out ? __fadd_rn(out_load(o), v) : v);
       }
     }

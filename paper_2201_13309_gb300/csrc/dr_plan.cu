@@ -509,12 +509,13 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
                               : pixels_smem_bytes(K, kc * n, B, tc, f64);
   };
   if (intervals) {
-    // 8 pixels x all steps per CTA; bins in windows of int32 accumulators,
-    // all bins in one window for three or two CTAs per SM where they fit
+    // 32 pixels x all steps per CTA; bins in windows of int32 accumulators
+    // sized for two CTAs per SM (one when a window would hold fewer than 256
+    // bins)
     t.ppt = 1;
     t.tile_cols = kIntervalTile;
     t.bin_groups = 1;
-    p->threads = 512;  // two warps per pixel
+    p->threads = 512;  // lane = pixel, warp = a chunk of intervals
     if (K > 65535) {
       delete p;
       set_error("dr_plan: the interval kernel takes at most 65535 steps");
@@ -580,11 +581,11 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
     return DR_ERR_UNSUPPORTED;
   }
   if (intervals) {
-    const size_t fixed = (size_t)intervals_smem(K, t.kc * t.nchunks, B, 0, f64);
+    const bool per_pixel = !rows_shared;
+    const size_t fixed = (size_t)intervals_smem(K, t.kc * t.nchunks, B, 0, f64, per_pixel);
     const size_t per_bin = (size_t)kIntervalTile * 4;
-    size_t budget = (size_t)(kSmemPerSm / 3 - 1024);
-    if (fixed + per_bin * B > budget) budget = (size_t)(kSmemPerSm / 2 - 1024);
-    if (fixed + per_bin * 32 > budget) budget = (size_t)kSmemPerCtaMax;
+    size_t budget = (size_t)(kSmemPerSm / 2 - 1024);
+    if (fixed + per_bin * (size_t)std::min(B, 256) > budget) budget = (size_t)kSmemPerCtaMax;
     const long long win = fixed < budget ? (long long)((budget - fixed) / per_bin) : 0;
     if (win < std::min(B, 32)) {
       delete p;
@@ -594,7 +595,7 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
     }
     p->window = (int)std::min<long long>(win, B);
     t.bin_groups = p->window;
-    p->smem_bytes = intervals_smem(K, t.kc * t.nchunks, B, p->window, f64);
+    p->smem_bytes = intervals_smem(K, t.kc * t.nchunks, B, p->window, f64, per_pixel);
   } else {
     p->smem_bytes = smem_for(t.tile_cols);
   }

@@ -139,7 +139,7 @@ def test_forced_per_pixel_geometry(cols):
     for s in (sc, back):
         plan, out = run(s, force_intervals=True)
         info = plan.info()
-        assert (info["kernel"], info["tile_cols"]) == ("intervals", 8)
+        assert (info["kernel"], info["tile_cols"]) == ("intervals", 32)
         assert_parity(out.cpu().numpy(), O.reconstruct(s.geom, s.wires, s.images, s.edges),
                       s.images)
 
