@@ -273,12 +273,16 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
       float w[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) w[u] = __fmul_rn(sign, iv_pow2(-iv_grid(ssum[p0 + u])));
-      for (int q = tid; q < nwin / 4; q += NT) {
-        const int4 a = reinterpret_cast<const int4 *>(acc)[DR_IDX(q, window * TC / 4, c.err)];
-        OutT *o = DR_PTR(out + (size_t)(wb0 + q / (TC / 4)) * plane + (size_t)row * c.W + c0 + p0,
-                         out, plane * B - 3, c.err);
-        st_cs4(o, __fmul_rn(__int2float_rn(a.x), w[0]), __fmul_rn(__int2float_rn(a.y), w[1]),
-               __fmul_rn(__int2float_rn(a.z), w[2]), __fmul_rn(__int2float_rn(a.w), w[3]));
+      // thread tid stores bins wb0 + tid / (TC / 4) + i * NT / (TC / 4)
+      const int4 *pq = reinterpret_cast<const int4 *>(acc) + tid;
+      const int4 *const pq_end = reinterpret_cast<const int4 *>(acc) + nwin / 4;
+      OutT *o = out + (size_t)(wb0 + tid / (TC / 4)) * plane + (size_t)row * c.W + c0 + p0;
+      const size_t o_step = (size_t)(NT / (TC / 4)) * plane;
+      for (; pq < pq_end; pq += NT, o += o_step) {
+        const int4 a = *DR_PTR(pq, reinterpret_cast<const int4 *>(acc), window * TC / 4, c.err);
+        st_cs4(DR_PTR(o, out, plane * B - 3, c.err), __fmul_rn(__int2float_rn(a.x), w[0]),
+               __fmul_rn(__int2float_rn(a.y), w[1]), __fmul_rn(__int2float_rn(a.z), w[2]),
+               __fmul_rn(__int2float_rn(a.w), w[3]));
       }
     } else {
       const float w = __fmul_rn(sign, iv_pow2(-iv_grid(ssum[lc])));
