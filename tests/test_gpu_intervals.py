@@ -204,3 +204,18 @@ def test_both_edges_mixed_depths():
     assert (info["kernel"], info["parts"]) == ("intervals", 2)
     assert_parity(out.cpu().numpy(),
                   O.reconstruct(sc.geom, sc.wires, sc.images, sc.edges, "both"), sc.images)
+
+
+def test_per_pixel_geometry_in_several_windows():
+    """Rotated detector (depths per pixel) with more bins than one window
+    holds, a ragged last tile of 32 pixels (70 columns), reversed travel."""
+    sc = synth.spot_scan(27, 3, 70, 101, 6, -60.0, 60.0, 0.7, rotate_deg=12.0,
+                         depth_range=(-0.03, 0.03))
+    sc.edges = synth.bin_edges(-150.0, 150.0, 0.05)
+    back = synth.Scan(sc.geom, sc.wires[::-1].copy(), sc.edges, sc.images[::-1].copy())
+    for s in (sc, back):
+        plan, out = run(s, force_intervals=True)
+        info = plan.info()
+        assert info["kernel"] == "intervals" and info["bin_groups"] < info["B"]
+        assert_parity(out.cpu().numpy(), O.reconstruct(s.geom, s.wires, s.images, s.edges),
+                      s.images)
