@@ -901,6 +901,11 @@ def main():
     ap.add_argument("--rotate", type=float, default=0.0,
                     help="rotate the detector in its plane (degrees): per-pixel depths")
     ap.add_argument("--tilt", type=float, default=0.0, help="tilt the detector about x (degrees)")
+    ap.add_argument("--wire-climb", type=float, default=0.0,
+                    help="wire also moves across the beam (um per step along y): depths "
+                         "of some pixels then run in both directions (interval kernel)")
+    ap.add_argument("--wire-jitter", type=float, default=0.0,
+                    help="seeded normal jitter of the wire centre across the beam (um)")
     ap.add_argument("--intervals", action="store_true",
                     help="use the interval kernel (depths in any order) on the same scan")
     ap.add_argument("--rows", type=int, default=2048,
@@ -959,6 +964,11 @@ def main():
     if args.rotate or args.tilt:
         spec.geom = synth.detector_geometry(2048, 2048, rotate_deg=args.rotate,
                                             tilt_deg=args.tilt)
+    if args.wire_climb or args.wire_jitter:
+        rng = np.random.Generator(np.random.PCG64(7))
+        spec.wires = spec.wires.copy()
+        spec.wires[:, 1] += (args.wire_climb * 1e-3 * np.arange(spec.K)
+                             + rng.normal(0.0, args.wire_jitter * 1e-3, spec.K))
     if args.rows != spec.geom["rows"]:
         spec.geom = dict(spec.geom, rows=args.rows)
         keep = spec.scat.spot_row < args.rows - 2
@@ -985,16 +995,18 @@ def main():
     t_plan = time.perf_counter()
     dr.Plan(spec.geom, spec.wires, spec.edges, force_intervals=args.intervals).close()
     plan_ms = (time.perf_counter() - t_plan) * 1e3
+    tuned = None
     if args.intervals:
         plan = dr.Plan(spec.geom, spec.wires, spec.edges, force_intervals=True)
-        tuned = None
     elif args.tile_cols:
         plan = dr.Plan(spec.geom, spec.wires, spec.edges, tile_cols=args.tile_cols,
                        bin_groups=args.bin_groups)
-        tuned = None
     else:
-        plan, tuned = autotune.tuned_plan(spec.geom, spec.wires, spec.edges, images, out=out,
-                                          use_cache=not args.retune)
+        plan = dr.Plan(spec.geom, spec.wires, spec.edges)
+        if plan.info()["kernel"] != "intervals":  # (depths in both directions: no shape to tune)
+            plan.close()
+            plan, tuned = autotune.tuned_plan(spec.geom, spec.wires, spec.edges, images, out=out,
+                                              use_cache=not args.retune)
     info = plan.info()
     stream = torch.cuda.Stream(dev)
     P = spec.P
@@ -1118,11 +1130,16 @@ def main():
                        + (f"; detector rotated {args.rotate} deg, tilted {args.tilt} deg"
                           if args.rotate or args.tilt else "")
                        + ("; interval kernel (depths in any order) forced"
-                          if args.intervals else ""), "pixels": P, "wire_steps": spec.K,
+                          if args.intervals else "")
+                       + (f"; wire also moving across the beam ({args.wire_climb} um per step, "
+                          f"{args.wire_jitter} um jitter, seed 7)"
+                          if args.wire_climb or args.wire_jitter else ""),
+                       "pixels": P, "wire_steps": spec.K,
                        "bins": spec.B, "parallelism": f"replicas x{world}",
                        "l2": f"input ({2 * units_per_step / 1e9:.2f} GB) and output "
                              f"({4 * P * spec.B / 1e9:.1f} GB) larger than L2; no flush",
                        "kernel": info["kernel"], "depth_form": info["depth_form"],
+                       "geometry": "fp64" if info["geom_precision"] else "fp32",
                        "plan_ms": round(plan_ms, 1),
                        "one_step_per_bin": info["one_step_per_bin"],
                        "tile_cols": info["tile_cols"],

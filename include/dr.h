@@ -158,7 +158,10 @@ typedef struct {
  * interval kernel also takes scans that the running-sum kernels cannot
  * (depth steps too fine for their fixed-point grid, tiles too large for
  * shared memory), unless options give tile_cols or bin_groups: a launch
- * shape that does not fit is then reported (DR_ERR_UNSUPPORTED).  The wire
+ * shape that does not fit is then reported (DR_ERR_UNSUPPORTED).  With FP32
+ * geometry the interval kernel apportions each interval shorter than its
+ * positions' grid resolves (next to a turning point of the depths, a
+ * repeated wire position) with that interval's depths in FP64.  The wire
  * must travel along the beam between its first and last centre
  * (DR_ERR_GEOMETRY otherwise).
  *   wire_centres  host [K][3] FP64, K >= 2

@@ -35,6 +35,11 @@
 // M in absolute value, up to FP32 rounding), and a part is rounded by at most
 // M 2^-30.  Integer sums do not depend on the order of the atomics, so the
 // result is deterministic.
+// FP32 positions carry a few units of their fixed-point grid.  An interval
+// shorter than kMinStepUnits (a step next to a turning point of the depths,
+// a repeated wire position) could then put its difference on the wrong side
+// of a bin edge, so its two depths are computed again in FP64 from the plan's
+// FP64 constants and it is apportioned against the FP64 edges by itself.
 #pragma once
 
 #include "dr_device.cuh"
@@ -47,16 +52,21 @@ __device__ __forceinline__ float iv_pow2(int q) { return __int_as_float((127 + q
 // the grid exponent q of a pixel whose sum of |dI| is M: M 2^q < 2^29
 __device__ __forceinline__ int iv_grid(uint32_t M) { return 29 - (32 - __clz(M)); }
 // 1 / (b - a) for a < b, and the position of e in [a, b] as a fraction (e
-// clamped to the interval by the caller: a <= e <= b)
+// clamped to the interval by the caller: a <= e <= b).  FP64 positions: the
+// differences are taken in FP64 (exact where the positions are close) and
+// the fraction in FP32, as for the fixed-point positions, so that the FP64
+// pipe does two subtractions per step and bin, not a division.
 __device__ __forceinline__ float iv_inv_len(int32_t lo, int32_t hi) {
   return rcp_approx(__uint2float_rn((uint32_t)hi - (uint32_t)lo));
 }
-__device__ __forceinline__ double iv_inv_len(double lo, double hi) { return 1.0 / (hi - lo); }
+__device__ __forceinline__ float iv_inv_len(double lo, double hi) {
+  return rcp_approx(__double2float_rn(hi - lo));
+}
 __device__ __forceinline__ float iv_frac(int32_t e, int32_t lo, float inv) {
   return fminf(__fmul_rn(__uint2float_rn((uint32_t)e - (uint32_t)lo), inv), 1.f);
 }
-__device__ __forceinline__ float iv_frac(double e, double lo, double inv) {
-  return (float)fmin((e - lo) * inv, 1.0);
+__device__ __forceinline__ float iv_frac(double e, double lo, float inv) {
+  return fminf(__fmul_rn(__double2float_rn(e - lo), inv), 1.f);
 }
 
 // Shared-memory layout (intervals_smem): [0, 128) mbarrier, the image tile
@@ -174,7 +184,54 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
     return lo;
   };
 
+  constexpr bool kFx = std::is_same<Geo, GeoFx>::value;
+  // intervals apportioned by themselves: zero length, and with FP32
+  // positions anything shorter than kMinStepUnits
+  auto is_short = [](pos_t a, pos_t b) {
+    if constexpr (kFx) return (uint32_t)(a < b ? b - a : a - b) < (uint32_t)kMinStepUnits;
+    return !(a < b) && !(b < a);
+  };
   float q_scale = 0.f;  // 2^q of pixel lc, read once the sums are complete
+  // Interval m of pixel lc by itself, dI != 0, into the bins of the window
+  // [wb0, wb1).  A zero-length interval puts dI into the bin [e_j, e_{j+1})
+  // holding its depth; a longer one spreads it by overlap.  With FP32
+  // positions the depths and edges are the FP64 ones (a binary search on the
+  // FP64 edges); a0 is the interval's first position on the kernel's grid.
+  auto short_interval = [&](int m, pos_t a0, int dI, int wb0, int wb1) {
+    if constexpr (kFx) {
+      const GroupD &gd = c.grp64[pixel_groups ? row * c.W + c0 + lc : row];
+      const double d0 = depth_f64(gd, c.stp64[m], c), d1 = depth_f64(gd, c.stp64[m + 1], c);
+      const double lo = fmin(d0, d1), hi = fmax(d0, d1);
+      int j = 0, jh = B;  // first bin: the last edge <= lo, or 0
+      if (!(c.e64[0] <= lo)) {
+        j = -1;
+      } else {
+        while (j < jh) {
+          const int mid = (j + jh + 1) >> 1;
+          if (c.e64[mid] <= lo) j = mid; else jh = mid - 1;
+        }
+      }
+      if (lo == hi) {
+        if (j >= wb0 && j < wb1 && j < B)
+          atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
+                    __float2int_rn(__fmul_rn((float)dI, q_scale)));
+        return;
+      }
+      const double inv = 1.0 / (hi - lo);
+      auto P = [&](double e) { return (double)dI * fmin(fmax((e - lo) * inv, 0.0), 1.0); };
+      for (j = max(j, wb0); j < wb1 && c.e64[j] < hi; ++j) {
+        const float v = (float)(P(c.e64[j + 1]) - P(c.e64[j]));
+        if (v != 0.f)
+          atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
+                    __float2int_rn(__fmul_rn(v, q_scale)));
+      }
+    } else {  // FP64 positions: only zero-length intervals come here
+      const int j = count_le(a0) - 1;
+      if (j >= wb0 && j < wb1)
+        atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
+                  __float2int_rn(__fmul_rn((float)dI, q_scale)));
+    }
+  };
   for (int wb0 = 0; wb0 < B; wb0 += window) {
     const int wb1 = min(wb0 + window, B);
     const int nwin = (wb1 - wb0) * TC;  // 32 accumulators per bin
@@ -239,16 +296,16 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
     // the chunk splits into strictly monotone runs and zero-length
     // intervals, and each run is walked once over the bins it spans; a chunk
     // whose depths miss the window is skipped whole
-    if (has_chunk && cmax >= ewlo && cmin < ewhi) {
+    // (FP32 positions: a margin of kMinStepUnits for the short intervals'
+    // FP64 depths)
+    const pos_t margin = kFx ? (pos_t)kMinStepUnits : (pos_t)0;
+    if (has_chunk && cmax + margin >= ewlo && cmin - margin < ewhi) {
       for (int m = m0; m < m1;) {
         const pos_t a = spos[DR_IDX(m * PS + lcs, K * PS, c.err)],
                     b = spos[DR_IDX((m + 1) * PS + lcs, K * PS, c.err)];
-        if (!(a < b) && !(b < a)) {  // zero length: the bin [e_j, e_{j+1}) holding a
+        if (is_short(a, b)) {
           const int dI = step_dI(m);
-          const int j = count_le(a) - 1;
-          if (dI != 0 && j >= wb0 && j < wb1)
-            atomicAdd(&acc[DR_IDX((j - wb0) * TC + lc, window * TC, c.err)],
-                      __float2int_rn(__fmul_rn((float)dI, q_scale)));
+          if (dI != 0) short_interval(m, a, dI, wb0, wb1);
           ++m;
           continue;
         }
@@ -256,7 +313,7 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
         int n = m + 1;  // the run: intervals m .. n - 1
         for (pos_t prev = b; n < m1; ++n) {
           const pos_t nx = spos[DR_IDX((n + 1) * PS + lcs, K * PS, c.err)];
-          if (up ? !(prev < nx) : !(nx < prev)) break;
+          if ((up ? !(prev < nx) : !(nx < prev)) || is_short(prev, nx)) break;
           prev = nx;
         }
         iv_run(m, n, up);

@@ -421,9 +421,10 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   const double scale = std::ldexp(1.0, shift);
   if (minstep == 1e300) minstep = 0.0;  // interval kernel, no nonzero step seen
   // FP32 geometry positions carry a few grid units of error, so an interval
-  // must span many units (zero-length intervals are exact); FP64 geometry
+  // of the running-sum kernels must span many units; the interval kernel
+  // apportions its shorter intervals with FP64 depths, and FP64 geometry
   // computes positions and fractions in FP64
-  if (P > 0 && opt.geom_precision == DR_GEOM_FP32 && minstep > 0.0 &&
+  if (P > 0 && !intervals && opt.geom_precision == DR_GEOM_FP32 && minstep > 0.0 &&
       minstep * scale < kMinStepUnits) {
     set_error("dr_plan: depth steps (%.3g mm) too small for the fixed-point grid", minstep);
     return DR_ERR_UNSUPPORTED;

@@ -76,6 +76,8 @@ def test_plan_rejects_bad_inputs(lib):
     fine = synth.wire_path(5, dz=1e-10)                          # 0.1 pm steps
     st, msg = _plan_status(g, fine, e)
     assert st == 8 and "too small" in msg                        # FP32 grid limit
+    # (on a GPU the interval kernel takes such a scan, its short intervals
+    # with FP64 depths: test_gpu_intervals.py)
     # Repeated positions and depths running against the wire's travel are
     # valid plans (the interval kernel): they get past validation to the
     # device allocation, tested in test_gpu_intervals.py.

@@ -256,13 +256,16 @@ def test_autotuner_picks_a_valid_shape(tmp_path, monkeypatch):
     assert again["cached"] and again["tile_cols"] == best["tile_cols"]
 
 
-def test_fp64_geometry_takes_sub_grid_steps():
-    """Steps of 0.2 pm are below what FP32 geometry's position grid holds
-    (refused, also by the interval kernel); FP64 geometry takes them."""
+def test_sub_grid_steps():
+    """Steps of 0.2 pm are below what FP32 geometry's position grid holds:
+    the running-sum kernels refuse them and the interval kernel takes the
+    scan, every interval with its depths in FP64; FP64 geometry takes them
+    in the rows kernel."""
     sc = synth.tiny_scan(41, rows=4, cols=16, K=21)
     sc.wires = synth.wire_path(21, dz=2e-10)
-    with pytest.raises(dr.DrError):
-        dr.Plan(sc.geom, sc.wires, sc.edges)
+    plan, out = run(sc)
+    assert (plan.info()["kernel"], plan.info()["geom_precision"]) == ("intervals", 0)
+    assert_parity(out.cpu().numpy(), ref_of(sc), sc.images)
     plan, out = run(sc, geom_precision="fp64")
     assert plan.info()["kernel"] == "rows"
     assert_parity(out.cpu().numpy(), ref_of(sc), sc.images, tol=1e-6)
