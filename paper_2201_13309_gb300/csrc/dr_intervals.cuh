@@ -191,6 +191,11 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
     if constexpr (kFx) return (uint32_t)(a < b ? b - a : a - b) < (uint32_t)kMinStepUnits;
     return !(a < b) && !(b < a);
   };
+  // b lies above a by an interval that is not short
+  auto longer = [](pos_t a, pos_t b) {
+    if constexpr (kFx) return b - a >= (pos_t)kMinStepUnits;
+    return a < b;
+  };
   float q_scale = 0.f;  // 2^q of pixel lc, read once the sums are complete
   // Interval m of pixel lc by itself, dI != 0, into the bins of the window
   // [wb0, wb1).  A zero-length interval puts dI into the bin [e_j, e_{j+1})
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
         int n = m + 1;  // the run: intervals m .. n - 1
         for (pos_t prev = b; n < m1; ++n) {
           const pos_t nx = spos[DR_IDX((n + 1) * PS + lcs, K * PS, c.err)];
-          if ((up ? !(prev < nx) : !(nx < prev)) || is_short(prev, nx)) break;
+          if (!(up ? longer(prev, nx) : longer(nx, prev))) break;
           prev = nx;
         }
         iv_run(m, n, up);
