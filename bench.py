@@ -849,7 +849,7 @@ def run_pixels(args, spec, images, dev):
     flat = act.reshape(-1)
     vals = flat.cpu().numpy()
     rows = []
-    for pct in (25, 50, 100):
+    for pct in (25, 50, 75, 100):
         thr = float(np.percentile(vals, 100 - pct)) if pct < 100 else -1.0
         sel_ms = t(lambda: dr.select_pixels(flat, thr))
         idx, n = dr.select_pixels(flat, thr)

@@ -1359,12 +1359,20 @@ constexpr int kSelChunk = 4096;  // pixels per block in the compaction kernels
 // (k, f) entries and only the bins in the row's data range touch the images;
 // otherwise it runs the per-pixel merge-walk of pixels_kernel on images read
 // from global memory.  Both give the full reconstruction's values bitwise.
+// A lane's image values come from global memory kSelBuf steps at a time
+// into its own column of a shared-memory buffer, so that many loads are in
+// flight (one at a time as the walk reached each step left the kernel
+// waiting on memory latency).
+constexpr int kSelBuf = 16;
+constexpr int kSelThreads = 256;
+
 template <class Geo, class OutT>
-__global__ void __launch_bounds__(256) selected_kernel(const Consts c, int kernel,
+__global__ void __launch_bounds__(kSelThreads) selected_kernel(const Consts c, int kernel,
                                                        const uint16_t *__restrict__ img,
                                                        const int32_t *__restrict__ idx, int n,
                                                        OutT *__restrict__ out) {
   using pos_t = typename Geo::pos_t;
+  __shared__ float sbuf[kSelBuf][kSelThreads];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int p = idx[i], K = c.K, B = c.B;
@@ -1372,6 +1380,21 @@ __global__ void __launch_bounds__(256) selected_kernel(const Consts c, int kerne
   const int row = p / c.W;
   const bool rev = c.reverse != 0;
   auto px = [&](int k) { return biased(__ldg(img + (size_t)(rev ? K - 1 - k : k) * plane + p)); };
+  float *const mybuf = &sbuf[0][threadIdx.x];
+  int kb = 0, kend = 0;  // steps [kb, kend) are in this lane's buffer
+  // image value of step k (k, k + 1 < K); refills the buffer from step k
+  auto val = [&](int k) {
+    if (k < kb || k >= kend) {
+      float v[kSelBuf];
+#pragma unroll
+      for (int s = 0; s < kSelBuf; ++s) v[s] = k + s < K ? px(k + s) : 0.f;
+#pragma unroll
+      for (int s = 0; s < kSelBuf; ++s) mybuf[s * kSelThreads] = v[s];
+      kb = k;
+      kend = min(k + kSelBuf, K);
+    }
+    return mybuf[(k - kb) * kSelThreads];
+  };
   const float sign = c.out_sign;
   const float I0 = px(0);
   OutT *o = out + i;
@@ -1388,9 +1411,9 @@ __global__ void __launch_bounds__(256) selected_kernel(const Consts c, int kerne
         if (kcur >= 0 && kf.x == kcur + 1) {
           Ik = Ik1;
         } else {
-          Ik = px(kf.x);
+          Ik = val(kf.x);
         }
-        Ik1 = px(kf.x + 1);
+        Ik1 = val(kf.x + 1);
         kcur = kf.x;
       }
       return __fmaf_rn(__int_as_float(kf.y), __fsub_rn(Ik, Ik1), __fsub_rn(I0, Ik));
@@ -1414,7 +1437,7 @@ __global__ void __launch_bounds__(256) selected_kernel(const Consts c, int kerne
   const pos_t tlast = Geo::depth(g, steps[K - 1], c);
   const float zero = __fmul_rn(sign, 0.f);
   auto inv = Geo::inv_len(t0, t1);
-  float Ik = I0, Ik1 = px(1), Fp = 0.f;
+  float Ik = I0, Ik1 = val(1), Fp = 0.f;
   pos_t ep = 0;
   for (int j = 0; j <= B; ++j) {
     const pos_t e = Geo::edge(c, j);
@@ -1424,7 +1447,7 @@ __global__ void __launch_bounds__(256) selected_kernel(const Consts c, int kerne
       t1 = Geo::depth(g, steps[k + 1], c);
       inv = Geo::inv_len(t0, t1);
       Ik = Ik1;
-      Ik1 = px(k + 1);
+      Ik1 = val(k + 1);
     }
     const float f = Geo::frac(e, t0, t1, inv);
     const float F = __fmaf_rn(f, __fsub_rn(Ik, Ik1), __fsub_rn(I0, Ik));

@@ -1125,11 +1125,12 @@ extern "C" dr_status dr_reconstruct_selected(const dr_plan_t *p, const uint16_t 
   const bool bf16 = p->out_dtype == DR_OUT_BF16;
   // Staged tiles load every image row segment that holds a listed pixel and
   // split the listed pixels' bins over the CTA's threads; they pay off when
-  // most pixels are listed (measured on the full-detector scan: the per-lane
-  // walk, images read from global memory, is faster up to about half of the
-  // pixels, where the staged tiles' short compacted output runs per tile
-  // leave partial 32-byte sectors).
-  const bool dense = (double)n >= 0.6 * (double)p->rows * p->cols;
+  // nearly all pixels are listed (measured on the full-detector scan: the
+  // per-lane walk, images read from global memory in runs of steps, is
+  // faster up to at least three quarters of the pixels, where the staged
+  // tiles' short compacted output runs per tile leave partial 32-byte
+  // sectors; the staged tiles win at all pixels).
+  const bool dense = (double)n >= 0.9 * (double)p->rows * p->cols;
   if (dense && p->kernel == DR_KERNEL_ROWS && p->c.tab && tma_usable(p, img)) {
     // staged: one CTA per (row, tile of at most 128 columns, two CTAs per
     // SM), 512 threads (listed pixels x bin groups)
@@ -1160,21 +1161,21 @@ extern "C" dr_status dr_reconstruct_selected(const dr_plan_t *p, const uint16_t 
     if (e != cudaSuccess) return cuda_fail("dr_reconstruct_selected", e);
     return DR_OK;
   }
-  const int blocks = (n + 255) / 256;
+  const int blocks = (n + kSelThreads - 1) / kSelThreads;
   if (p->geom_prec == DR_GEOM_FP64) {
     if (bf16)
-      selected_kernel<GeoF64, __nv_bfloat16><<<blocks, 256, 0, st>>>(
+      selected_kernel<GeoF64, __nv_bfloat16><<<blocks, kSelThreads, 0, st>>>(
           p->c, p->kernel, img, idx, n, (__nv_bfloat16 *)out);
     else
-      selected_kernel<GeoF64, float><<<blocks, 256, 0, st>>>(p->c, p->kernel, img, idx, n,
-                                                             (float *)out);
+      selected_kernel<GeoF64, float><<<blocks, kSelThreads, 0, st>>>(p->c, p->kernel, img, idx,
+                                                                     n, (float *)out);
   } else {
     if (bf16)
-      selected_kernel<GeoFx, __nv_bfloat16><<<blocks, 256, 0, st>>>(
+      selected_kernel<GeoFx, __nv_bfloat16><<<blocks, kSelThreads, 0, st>>>(
           p->c, p->kernel, img, idx, n, (__nv_bfloat16 *)out);
     else
-      selected_kernel<GeoFx, float><<<blocks, 256, 0, st>>>(p->c, p->kernel, img, idx, n,
-                                                            (float *)out);
+      selected_kernel<GeoFx, float><<<blocks, kSelThreads, 0, st>>>(p->c, p->kernel, img, idx,
+                                                                    n, (float *)out);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail("dr_reconstruct_selected", e);

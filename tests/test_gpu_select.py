@@ -35,7 +35,7 @@ def test_selection_sweep(rotate):
     plan = dr.Plan(sc.geom, sc.wires, sc.edges)
     full = plan.reconstruct(img).reshape(sc.B, -1)
     flat = act.reshape(-1)
-    for pct in (3, 25, 50, 70, 100):   # lists under 60% walk, denser ones are staged
+    for pct in (3, 25, 50, 70, 95, 100):   # lists under 90% walk, denser ones are staged
         thr = float(np.percentile(want, 100 - pct)) if pct < 100 else -1.0
         idx, n = dr.select_pixels(flat, thr)
         ref_idx = np.nonzero(want.reshape(-1) >= thr)[0]
