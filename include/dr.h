@@ -272,15 +272,18 @@ dr_status dr_selftest_wait_timeout(int32_t *d_status, double wait_ms, dr_stream_
 /* ---- Many scans in one persistent launch ---------------------------------
  * A batch reconstructs several scans (each with its own plan, image stack and
  * output; different ROI sizes, step and bin counts) in ONE launch of a
- * persistent kernel: every CTA takes (scan, row, tile) work items from a device
- * counter until none are left, biggest items first, so uneven scans do not
- * leave the GPU idle between per-scan launches.  The counter reset and the
- * launch are captured into a CUDA graph at creation; dr_batch_launch replays
- * it.  Jobs must use rows-kernel plans (columns along the wire axis) with FP32
- * geometry, widths that are multiples of 8, 16-byte aligned buffers and one
- * output type.  The buffers are bound at creation: a batch always reads and
- * writes the same device buffers (refill the image buffers between launches).
- * The result of every scan is bitwise identical to dr_reconstruct's. */
+ * persistent kernel: every CTA takes work items (a tile column of four rows
+ * of one scan) from a device counter until none are left, biggest items
+ * first, so uneven scans do not leave the GPU idle between per-scan
+ * launches.  The counter reset and the launch are captured into a CUDA graph
+ * at creation; dr_batch_launch replays it.  Jobs must use single-run,
+ * single-edge plans of the rows or per-pixel kernel (not the interval
+ * kernel) with FP32 geometry, widths that are multiples of 8, 16-byte aligned
+ * buffers and one output type (DR_ERR_UNSUPPORTED, naming the job and the
+ * reason, otherwise).  The buffers are bound at creation: a batch always
+ * reads and writes the same device buffers (refill the image buffers between
+ * launches).  The result of every scan is bitwise identical to
+ * dr_reconstruct's. */
 typedef struct {
   const dr_plan_t *plan;
   const uint16_t *d_images;   /* [K][rows][cols] of the plan, device */

@@ -39,7 +39,7 @@ namespace {
 constexpr int kBatchThreads = 512;
 // tiles per work item (consecutive rows, same columns): the work counter's
 // round trip and the scan lookup are paid once per item
-constexpr int kRowsPerItem = 2;
+constexpr int kRowsPerItem = 4;
 
 void destroy(dr_batch_t *b) {
   if (!b) return;
