@@ -221,23 +221,30 @@ def test_per_pixel_geometry_in_several_windows():
                       s.images)
 
 
-@pytest.mark.parametrize("rotate", [0.0, 9.0])
-def test_steps_too_fine_for_fp32_positions(rotate):
+@pytest.mark.parametrize("rotate,edge,backward", [(0.0, "leading", False),
+                                                   (9.0, "leading", False),
+                                                   (9.0, "trailing", False),
+                                                   (0.0, "leading", True)])
+def test_steps_too_fine_for_fp32_positions(rotate, edge, backward):
     """A step of 1 pm is below what the FP32 positions' grid resolves: the
     interval kernel apportions that interval with its depths in FP64.  A bin
     edge is put inside the short interval of row 0, so its difference is
-    split between two bins; FP32 plan, within the FP32 bar of the oracle."""
+    split between two bins; FP32 plan, within the FP32 bar of the oracle;
+    trailing edge and a reversed scan included."""
     sc = synth.tiny_scan(28, rows=6, cols=40, K=41, rotate_deg=rotate)
     w = sc.wires.copy()
     w[20:, 2] -= 0.001 - 1e-9
     sc.wires = w
-    d = O.depths(sc.geom, sc.wires)
-    mid = 0.5 * (d[0, 0, 19] + d[0, 0, 20])
-    edges = synth.bin_edges(-50.0, 50.0, 1.0)
+    if backward:
+        sc = synth.Scan(sc.geom, sc.wires[::-1].copy(), sc.edges, sc.images[::-1].copy())
+    d = O.depths(sc.geom, sc.wires, edge)
+    k = 20 if backward else 19  # the short interval joins steps k and k + 1
+    mid = 0.5 * (d[0, 0, k] + d[0, 0, k + 1])
+    edges = synth.bin_edges(-50.0, 90.0, 1.0)
     j = int(np.searchsorted(edges, mid))
     sc.edges = edges + (mid - edges[j])
-    plan, out = run(sc)
+    plan, out = run(sc, edge=edge)
     info = plan.info()
     assert (info["kernel"], info["geom_precision"]) == ("intervals", 0)  # FP32
-    assert_parity(out.cpu().numpy(), O.reconstruct(sc.geom, sc.wires, sc.images, sc.edges),
-                  sc.images)
+    assert_parity(out.cpu().numpy(),
+                  O.reconstruct(sc.geom, sc.wires, sc.images, sc.edges, edge), sc.images)
