@@ -206,7 +206,10 @@ dr_status dr_reconstruct_host(const dr_plan_t *plan, const uint16_t *h_images,
  * (0 = as large as three slab buffers allow).  For each slab: one 2-D
  * host->device copy of its rows of every image, the reconstruction kernel,
  * and one 2-D device->host copy of its rows of every bin; three internal
- * streams overlap uploads, kernels and downloads across slabs.  h_images
+ * streams overlap uploads, kernels and downloads across slabs.  When h_out is
+ * pinned (page-locked and mapped) and the images are staged by TMA, the
+ * kernels store the bins straight into h_out instead (no download stage;
+ * plans of several runs or both edges keep the download).  h_images
  * [K][rows][cols] and h_out [B][rows][cols] are host memory (pinned for full
  * speed).  Ordered after prior work on stream; later work on stream waits
  * for the last download.  Calls are serialised by the library (one internal

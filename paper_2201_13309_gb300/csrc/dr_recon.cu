@@ -811,6 +811,22 @@ extern "C" dr_status dr_reconstruct_streamed(const dr_plan_t *p, const uint16_t 
   if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: fork", e);
   const int groups_per_row = p->pixel_groups ? W : 1;
   const int nslab = (H + slab_rows - 1) / slab_rows;
+  // When h_out is pinned (mapped into the device's address space) and the
+  // slabs are staged by TMA, the kernels store each slab's bins straight into
+  // h_out over the host link: the output crosses the link once with no
+  // download stage (full-detector scan: 86.7 ms for the kernel writing to
+  // the host against 94 ms for one device->host copy of the same bytes).  The
+  // kernels then take the whole scan's rows as their output plane.  Plans of
+  // several parts (which add to their output) keep the download.
+  unsigned char *h_out_dev = nullptr;
+  if (p->parts.empty() && tma_usable(p, static_cast<const uint16_t *>(d_ws))) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, h_out) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer)
+      h_out_dev = static_cast<unsigned char *>(at.devicePointer);
+    else
+      cudaGetLastError();  // an unregistered buffer: the download path
+  }
   for (int i = 0; i < nslab; ++i) {
     const int b = i % nbuf, r0 = i * slab_rows, n = std::min(slab_rows, H - r0);
     unsigned char *buf = static_cast<unsigned char *>(d_ws) + slab_bytes(slab_rows) * b;
@@ -824,7 +840,8 @@ extern "C" dr_status dr_reconstruct_streamed(const dr_plan_t *p, const uint16_t 
     if (e == cudaSuccess) e = cudaEventRecord(ss->up_done[b], ss->up);
     // kernel: after the upload, and after the previous download of this buffer
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->comp, ss->up_done[b], 0);
-    if (e == cudaSuccess && i >= nbuf) e = cudaStreamWaitEvent(ss->comp, ss->down_done[b], 0);
+    if (e == cudaSuccess && i >= nbuf && !h_out_dev)
+      e = cudaStreamWaitEvent(ss->comp, ss->down_done[b], 0);
     if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: upload", e);
     const size_t nparts = p->parts.empty() ? 1 : p->parts.size();
     for (size_t q = 0; q < nparts; ++q) {
@@ -833,15 +850,18 @@ extern "C" dr_status dr_reconstruct_streamed(const dr_plan_t *p, const uint16_t 
       dr_plan_t slab = *part;
       slab.parts.clear();
       slab.rows = n;
-      slab.c.H = n;
+      slab.c.H = h_out_dev ? H : n;  // rows of the output plane
       slab.c.grp = part->c.grp + (size_t)r0 * groups_per_row;
       slab.c.grp64 = part->c.grp64 + (size_t)r0 * groups_per_row;
       if (part->c.tab) slab.c.tab = part->c.tab + (size_t)r0 * part->c.tab_stride;
-      s = launch_reconstruct(&slab, dimg + (size_t)k0 * n * W, dout, ss->comp);
+      void *o = h_out_dev ? (void *)(h_out_dev + (size_t)r0 * W * osz) : dout;
+      s = launch_reconstruct(&slab, dimg + (size_t)k0 * n * W, o, ss->comp);
       if (s != DR_OK) return s;
     }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(ss->comp_done[b], ss->comp);
+    if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: kernel", e);
+    if (h_out_dev) continue;  // the kernel wrote the slab's bins to the host
     // download the slab's bins into rows r0.. of every output plane
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->down, ss->comp_done[b], 0);
     if (e == cudaSuccess)
@@ -851,8 +871,10 @@ extern "C" dr_status dr_reconstruct_streamed(const dr_plan_t *p, const uint16_t 
     if (e == cudaSuccess) e = cudaEventRecord(ss->down_done[b], ss->down);
     if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: download", e);
   }
-  // join: the caller's stream continues after the last download
-  e = cudaEventRecord(ss->down_done[0], ss->down);
+  // join: the caller's stream continues after the last download (or the
+  // last kernel when the kernels wrote to the host)
+  cudaStream_t last = h_out_dev ? ss->comp : ss->down;
+  e = cudaEventRecord(ss->down_done[0], last);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ss->down_done[0], 0);
   if (e != cudaSuccess) return cuda_fail("dr_reconstruct_streamed: join", e);
   return DR_OK;

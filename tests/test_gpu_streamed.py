@@ -61,3 +61,30 @@ def test_streamed_rejects_small_workspace():
     with pytest.raises(dr.DrError) as ex:
         plan.reconstruct_streamed(h_img, h_out, ws, slab_rows=4)
     assert ex.value.status == 5
+
+
+def test_streamed_download_path():
+    """A pageable host output (not mapped into the device's address space)
+    and a plan of two runs (a path that turns back) take the download stage
+    instead of the kernels writing to the host: bitwise the in-core result."""
+    sc = synth.tiny_scan(65, rows=13, cols=64, K=31)
+    plan = dr.Plan(sc.geom, sc.wires, sc.edges)
+    h_img = torch.from_numpy(np.ascontiguousarray(sc.images).view(np.int16)).pin_memory()
+    ref = plan.reconstruct(h_img.cuda()).cpu()
+    h_out = torch.full(tuple(ref.shape), float("nan"))  # pageable
+    ws = torch.empty(16 << 20, dtype=torch.uint8, device="cuda")
+    plan.reconstruct_streamed(h_img, h_out, ws, slab_rows=4)
+    torch.cuda.synchronize()
+    assert torch.equal(ref.view(torch.int32), h_out.view(torch.int32))
+    a = synth.wire_path(16)
+    b = synth.wire_path(11, z0=a[-1, 2], dz=-0.001)[1:]
+    wires = np.concatenate([a, b])
+    back = synth.Scan(sc.geom, wires, sc.edges, sc.images[:26])
+    plan2 = dr.Plan(back.geom, back.wires, back.edges)
+    assert plan2.info()["parts"] == 2
+    h_img2 = torch.from_numpy(np.ascontiguousarray(back.images).view(np.int16)).pin_memory()
+    ref2 = plan2.reconstruct(h_img2.cuda()).cpu()
+    h_out2 = torch.full(tuple(ref2.shape), float("nan")).pin_memory()
+    plan2.reconstruct_streamed(h_img2, h_out2, ws, slab_rows=5)
+    torch.cuda.synchronize()
+    assert torch.equal(ref2.view(torch.int32), h_out2.view(torch.int32))
