@@ -280,10 +280,10 @@ dr_status dr_selftest_wait_timeout(int32_t *d_status, double wait_ms, dr_stream_
  * first, so uneven scans do not leave the GPU idle between per-scan
  * launches.  The counter reset and the launch are captured into a CUDA graph
  * at creation; dr_batch_launch replays it.  Jobs must use single-run,
- * single-edge plans of the rows or per-pixel kernel (not the interval
- * kernel) with FP32 geometry, widths that are multiples of 8, 16-byte aligned
- * buffers and one output type (DR_ERR_UNSUPPORTED, naming the job and the
- * reason, otherwise).  The buffers are bound at creation: a batch always
+ * single-edge plans (rows, per-pixel or interval kernel) with FP32
+ * geometry, widths that are multiples of 8, 16-byte aligned buffers and one
+ * output type (DR_ERR_UNSUPPORTED, naming the job and the reason,
+ * otherwise).  The buffers are bound at creation: a batch always
  * reads and writes the same device buffers (refill the image buffers between
  * launches).  The result of every scan is bitwise identical to
  * dr_reconstruct's. */

@@ -110,9 +110,15 @@ def tune(geom, wires, edges, images, out=None, edge="leading", out_dtype="f32",
 def tuned_plan(geom, wires, edges, images, **kw):
     """A Plan with the autotuned launch shape.  A cached shape tuned on a
     scan of the same class may not fit this one's shared memory (more steps
-    in the same bucket); the scan is then tuned on its own."""
+    in the same bucket); the scan is then tuned on its own.  A scan that
+    takes the interval kernel (whose tile is fixed) is planned as it is."""
     plan_kw = {k: kw[k] for k in ("edge", "out_dtype", "geom_precision", "force_pixels")
                if k in kw}
+    first = dr.Plan(geom, wires, edges, **plan_kw)
+    if first.info()["kernel"] == "intervals":  # its tile shape is fixed: nothing to tune
+        return first, {"tile_cols": first.info()["tile_cols"], "bin_groups": 0, "ms": None,
+                       "candidates": [], "cached": False, "key": None}
+    first.close()
     best = tune(geom, wires, edges, images, **kw)
     try:
         plan = dr.Plan(geom, wires, edges, tile_cols=best["tile_cols"],

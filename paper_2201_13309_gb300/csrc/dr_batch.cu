@@ -15,7 +15,7 @@
 #include <numeric>
 #include <vector>
 
-#include "dr_device.cuh"
+#include "dr_batch.cuh"
 #include "dr_internal.h"
 
 struct dr_batch {
@@ -51,8 +51,10 @@ void destroy(dr_batch_t *b) {
 }
 
 template <class OutT>
-const void *batch_fn(bool poly_only) {
-  return poly_only ? (const void *)batch_kernel<OutT, true> : (const void *)batch_kernel<OutT, false>;
+const void *batch_fn(int set) {
+  return set == kSetPolyOnly ? (const void *)batch_kernel<OutT, kSetPolyOnly>
+         : set == kSetAll    ? (const void *)batch_kernel<OutT, kSetAll>
+                             : (const void *)batch_kernel<OutT, kSetRunningSum>;
 }
 
 }  // namespace
@@ -80,24 +82,22 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
   std::vector<BatchScan> desc(n);
   std::vector<double> cost(n);
   int smem_max = 0, out_dtype = -1;
-  bool poly_only = true;
+  bool poly_only = true, any_intervals = false;
   for (int i = 0; i < n; ++i) {
     const dr_plan_t *p = jobs[i].plan;
     if (!p) {
       set_error("dr_batch_create: job %d has no plan", i);
       return DR_ERR_INVALID_ARG;
     }
-    const bool rows = p->kernel == DR_KERNEL_ROWS;
+    const bool rows = p->kernel == DR_KERNEL_ROWS, iv = p->kernel == DR_KERNEL_INTERVALS;
     const char *why = !p->parts.empty() ? "a composite plan (monotone runs or both edges)"
-                      : (!rows && p->kernel != DR_KERNEL_PIXELS) ? "an interval-kernel plan"
-                      : p->geom_prec != DR_GEOM_FP32              ? "FP64 geometry"
-                      : p->cols % 8 != 0                          ? "a width not a multiple of 8"
-                      : (rows && p->tune.ppt != 4)                ? "one pixel per thread"
-                                                                  : nullptr;
+                      : p->geom_prec != DR_GEOM_FP32  ? "FP64 geometry"
+                      : p->cols % 8 != 0              ? "a width not a multiple of 8"
+                      : (rows && p->tune.ppt != 4)    ? "one pixel per thread"
+                                                      : nullptr;
     if (why) {
       set_error("dr_batch_create: job %d is %s; the batch runs single-run, single-edge plans "
-                "of the rows or per-pixel kernel with FP32 geometry on widths that are "
-                "multiples of 8",
+                "with FP32 geometry on widths that are multiples of 8",
                 i, why);
       return DR_ERR_UNSUPPORTED;
     }
@@ -117,8 +117,17 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
     // pixels per thread.  Per-pixel tiles: one pixel per lane, the bins
     // shared among nthreads / tile_cols threads per pixel.
     Tuning t = p->tune;
-    int smem = 0, lanes = 0;
-    if (rows) {
+    int smem = 0, lanes = 0, window = 0;
+    if (iv) {
+      // interval tiles keep the plan's 32 columns and step chunks; the bin
+      // window shrinks to the per-CTA budget if it must
+      lanes = kIntervalTile;
+      const int fixed = intervals_smem(p->K, t.kc * t.nchunks, p->B, 0, false, p->pixel_groups);
+      const int per_bin = kIntervalTile * 4;
+      window = std::min(p->window, std::max(0, (smem_budget - fixed) / per_bin));
+      if (window < std::min(p->B, 32)) window = p->window;  // reported below as not fitting
+      smem = intervals_smem(p->K, t.kc * t.nchunks, p->B, window, false, p->pixel_groups);
+    } else if (rows) {
       if (opt.max_tile_cols >= 32 && t.tile_cols > opt.max_tile_cols)
         t.tile_cols = opt.max_tile_cols / 32 * 32;
       for (;;) {
@@ -151,7 +160,7 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
       set_error("dr_batch_create: job %d (%d steps) does not fit in shared memory", i, p->K);
       return DR_ERR_UNSUPPORTED;
     }
-    t.bin_groups = nthreads / lanes;
+    t.bin_groups = iv ? window : nthreads / lanes;
     smem_max = std::max(smem_max, smem);
     BatchScan &d = desc[i];
     std::memset(&d, 0, sizeof(d));
@@ -161,21 +170,27 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
     d.t = t;
     d.tiles_per_row = (p->cols + t.tile_cols - 1) / t.tile_cols;
     d.rows_per_item = kRowsPerItem;
-    if (rows)
+    d.pixel_groups = p->pixel_groups;
+    d.window = window;
+    if (iv)
+      d.kind = kBatchIntervals;
+    else if (rows)
       d.kind = kBatchRows;
     else if (p->c.depth_mode == kDepthPoly)
       d.kind = p->one_adv ? kBatchPixelsPolyOneAdv : kBatchPixelsPoly;
     else
       d.kind = p->one_adv ? kBatchPixelsOneAdv : kBatchPixels;
     poly_only &= d.kind == kBatchPixelsPolyOneAdv || d.kind == kBatchPixelsPoly;
+    any_intervals |= iv;
     if (P > 0) {
       dr_plan_t tmp = *p;
       tmp.tune = t;
       dr_status s = make_tensor_map(&tmp, jobs[i].d_images, &d.tmap);
       if (s != DR_OK) return s;
     }
-    // per-pixel tiles cost about twice a rows tile of the same size
-    cost[i] = (double)t.tile_cols * p->B * (rows ? 1.0 : 2.0);
+    // per-pixel tiles cost about twice a rows tile of the same size, interval
+    // tiles about three times
+    cost[i] = (double)t.tile_cols * p->B * (rows ? 1.0 : iv ? 3.0 : 2.0);
   }
   // most expensive items first (the counter hands items out in order)
   std::vector<int> order(n);
@@ -201,8 +216,9 @@ extern "C" dr_status dr_batch_create(const dr_job *jobs, int32_t n,
   b->n_items = items;
   b->out_dtype = out_dtype;
   b->smem = smem_max;
-  const void *fn = out_dtype == DR_OUT_BF16 ? batch_fn<__nv_bfloat16>(poly_only)
-                                            : batch_fn<float>(poly_only);
+  const int set = any_intervals ? kSetAll : poly_only ? kSetPolyOnly : kSetRunningSum;
+  const void *fn = out_dtype == DR_OUT_BF16 ? batch_fn<__nv_bfloat16>(set)
+                                            : batch_fn<float>(set);
   dr_status s = allow_smem(fn);
   if (s != DR_OK) {
     destroy(b);

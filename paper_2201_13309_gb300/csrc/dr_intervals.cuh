@@ -72,15 +72,17 @@ __device__ __forceinline__ float iv_frac(double e, double lo, float inv) {
 // Shared-memory layout (intervals_smem): [0, 128) mbarrier, the image tile
 // [Kpad][32] uint16, the depths [K][32] (pixel_groups) or [K], the edges
 // [B + 1], the pixels' sums of |dI| [32], the accumulators [window][32].
-// (two CTAs per SM with FP32 geometry, one with FP64)
+// One tile: row `row`, columns c0 .. c0 + 31, all steps and bins.  The
+// mbarrier at smem[0] must be initialised (by thread 0 before the call, or
+// earlier with a barrier since); `parity` is its phase for this tile.
+// Returns false (for every thread) if the bounded TMA wait ran out.
 template <class Geo, class OutT, bool kTma>
-__global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
-    intervals_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *__restrict__ img,
-                     OutT *__restrict__ out, const Consts c, const Tuning t, int pixel_groups,
-                     int window) {
+__device__ __forceinline__ bool intervals_tile(const CUtensorMap *tmap, const uint16_t *img,
+                                               OutT *out, const Consts &c, const Tuning &t,
+                                               int pixel_groups, int window, int row, int c0,
+                                               unsigned char *smem, uint32_t parity) {
   using pos_t = typename Geo::pos_t;
   constexpr int TC = kIntervalTile;
-  extern __shared__ __align__(128) unsigned char smem[];
   const int K = c.K, B = c.B;
   const int Kpad = t.kc * t.nchunks;
   const int PS = pixel_groups ? TC : 1;  // depth columns
@@ -92,7 +94,6 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
   uint32_t *ssum = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(sedge) +
                                                 align16((size_t)(B + 1) * sizeof(pos_t)));
   int32_t *acc = reinterpret_cast<int32_t *>(ssum + TC);
-  const int row = blockIdx.y, c0 = blockIdx.x * TC;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int ncols = min(TC, c.W - c0);
   // thread = (pixel lc, chunk slot warp); with 32 pixels a slot is a warp
@@ -100,10 +101,7 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
   const int lcs = pixel_groups ? lc : 0;  // this pixel's depth column
   const bool valid = lc < ncols;
 
-  if constexpr (kTma) {
-    if (tid == 0) mbar_init(bar, 1);
-  }
-  stage_tile<kTma>(&tmap, img, simg, bar, c, t, row, c0);
+  stage_tile<kTma>(tmap, img, simg, bar, c, t, row, c0);
   {
     const auto *steps = Geo::steps(c);
     if (pixel_groups) {  // steps warp, warp + nw, ... of pixel lc, two at a time
@@ -127,8 +125,8 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
   if (tid < TC) ssum[tid] = 0u;
   __syncthreads();  // also makes the mbarrier initialisation visible
   if constexpr (kTma) {
-    const bool late = !mbar_wait_bounded(bar, 0, c.err);
-    if (__syncthreads_or(late)) return;
+    const bool late = !mbar_wait_bounded(bar, parity, c.err);
+    if (__syncthreads_or(late)) return false;
   }
 
   const bool rev = c.reverse != 0;
@@ -358,6 +356,24 @@ __global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
     }
     if (wb1 < B) __syncthreads();  // the window's accumulators are reused
   }
+  return true;
+}
+
+// One CTA per tile (grid: tiles along the row x rows); two CTAs per SM with
+// FP32 geometry, one with FP64.
+template <class Geo, class OutT, bool kTma>
+__global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
+    intervals_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *__restrict__ img,
+                     OutT *__restrict__ out, const Consts c, const Tuning t, int pixel_groups,
+                     int window) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  // thread 0 initialises the barrier and issues the copies; the others
+  // first poll it after the tile's first __syncthreads
+  if constexpr (kTma) {
+    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
+  }
+  intervals_tile<Geo, OutT, kTma>(&tmap, img, out, c, t, pixel_groups, window, blockIdx.y,
+                                  blockIdx.x * kIntervalTile, smem, 0u);
 }
 
 }  // namespace dr
