@@ -88,3 +88,12 @@ def test_streamed_download_path():
     plan2.reconstruct_streamed(h_img2, h_out2, ws, slab_rows=5)
     torch.cuda.synchronize()
     assert torch.equal(ref2.view(torch.int32), h_out2.view(torch.int32))
+
+
+def test_streamed_plain_loads_and_ragged_slab():
+    """A width whose rows are not 16-byte multiples (plain loads, so the
+    download path even with a pinned output) and a last slab shorter than
+    the others: bitwise the in-core result."""
+    sc = synth.tiny_scan(66, rows=11, cols=70, K=23)
+    ref, got = _case(sc, 4)
+    assert torch.equal(ref.view(torch.int32), got.view(torch.int32))
