@@ -69,13 +69,13 @@ __device__ __forceinline__ float iv_frac(double e, double lo, float inv) {
   return fminf(__fmul_rn(__double2float_rn(e - lo), inv), 1.f);
 }
 
-// Shared-memory layout (intervals_smem): [0, 128) mbarrier, the image tile
-// [Kpad][32] uint16, the depths [K][32] (pixel_groups) or [K], the edges
-// [B + 1], the pixels' sums of |dI| [32], the accumulators [window][32].
 // One tile: row `row`, columns c0 .. c0 + 31, all steps and bins.  The
 // mbarrier at smem[0] must be initialised (by thread 0 before the call, or
 // earlier with a barrier since); `parity` is its phase for this tile.
 // Returns false (for every thread) if the bounded TMA wait ran out.
+// Shared-memory layout (intervals_smem): [0, 128) mbarrier, the image tile
+// [Kpad][32] uint16, the depths [K][32] (pixel_groups) or [K], the edges
+// [B + 1], the pixels' sums of |dI| [32], the accumulators [window][32].
 template <class Geo, class OutT, bool kTma>
 __device__ __forceinline__ bool intervals_tile(const CUtensorMap *tmap, const uint16_t *img,
                                                OutT *out, const Consts &c, const Tuning &t,
