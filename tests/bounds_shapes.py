@@ -4,10 +4,12 @@ DR_LIBRARY pointing at libdr_checked.so).
 
 Each shape runs through the rows kernel, the per-pixel kernels (the
 polynomial form, and the depth-table form by asking for the exact form), the
-interval kernel, a persistent batch and the no-allocation entry point; after
-each, the plan's error word must be clear (dr_plan_check raises with the
-device-source line of the first index found out of range) and the result
-must match the FP64 oracle within the parity tolerance.
+interval kernel, a persistent batch and the no-allocation entry point, and
+the seeded random scans of every path kind through their plans' kernels in
+core and streamed; after each, the plan's error word must be clear
+(dr_plan_check raises with the device-source line of the first index found
+out of range) and the result must match the FP64 oracle within the parity
+tolerance.
 """
 import os
 import sys
@@ -66,10 +68,30 @@ def main():
             close(out, sc, edge)
             runs += 1
             info = plan.info()
-            if (sc.geom["cols"] % 8 == 0 and info["kernel"] in ("rows", "pixels")
-                    and (info["kernel"] == "pixels" or info["pixels_per_thread"] == 4)):
+            if (sc.geom["cols"] % 8 == 0 and info["parts"] == 1
+                    and (info["kernel"] != "rows" or info["pixels_per_thread"] == 4)):
                 jobs.append((plan, img, torch.full_like(out, float("nan")), sc, edge))
-    # one persistent batch over every rows and per-pixel job that it takes
+    # seeded random scans of every path kind (tests/test_gpu_random_paths.py),
+    # in core and streamed through two-row slabs into a pinned host output
+    from tests.test_gpu_random_paths import random_scan
+    ws = torch.empty(32 << 20, dtype=torch.uint8, device="cuda")
+    for seed in range(24):
+        sc, edge, _ = random_scan(seed)
+        try:
+            plan = dr.Plan(sc.geom, sc.wires, sc.edges, edge=edge)
+        except dr.DrError:
+            continue
+        h_img = torch.from_numpy(np.ascontiguousarray(sc.images).view(np.int16)).pin_memory()
+        out = plan.reconstruct(h_img.cuda())
+        h_out = torch.full(tuple(out.shape), float("nan")).pin_memory()
+        plan.reconstruct_streamed(h_img, h_out, ws, slab_rows=2)
+        torch.cuda.synchronize()
+        plan.check_device()
+        close(out, sc, edge)
+        close(h_out, sc, edge)
+        runs += 1
+    # one persistent batch over every job that it takes (rows, per-pixel and
+    # interval tiles)
     batch = dr.Batch([(p, i, o) for p, i, o, _, _ in jobs])
     batch.launch()
     torch.cuda.synchronize()
