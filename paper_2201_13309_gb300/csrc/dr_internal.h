@@ -17,6 +17,7 @@ struct dr_plan {
   int kernel;              // DR_KERNEL_ROWS / DR_KERNEL_PIXELS / DR_KERNEL_INTERVALS
   int pixel_groups;        // 1: geometry constants per pixel, 0: per row
   int window;              // interval kernel: bins per shared-memory window
+  int iv_ctas = 2;         // interval kernel: CTAs per SM its tile is sized for
   int out_dtype, geom_prec;
   int shift;
   double nb;               // |projected beam direction|: depth = t / nb

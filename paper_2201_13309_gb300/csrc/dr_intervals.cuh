@@ -359,10 +359,11 @@ __device__ __forceinline__ bool intervals_tile(const CUtensorMap *tmap, const ui
   return true;
 }
 
-// One CTA per tile (grid: tiles along the row x rows); two CTAs per SM with
-// FP32 geometry, one with FP64.
-template <class Geo, class OutT, bool kTma>
-__global__ void __launch_bounds__(512, Geo::kPixelsMinBlocks > 1 ? 2 : 1)
+// One CTA per tile (grid: tiles along the row x rows), kMinBlocks CTAs per
+// SM: three (40 registers) when the plan's tile fits three times, else two
+// with FP32 geometry (64 registers), one with FP64.
+template <class Geo, class OutT, bool kTma, int kMinBlocks>
+__global__ void __launch_bounds__(512, kMinBlocks)
     intervals_kernel(const __grid_constant__ CUtensorMap tmap, const uint16_t *__restrict__ img,
                      OutT *__restrict__ out, const Consts c, const Tuning t, int pixel_groups,
                      int window) {

@@ -511,8 +511,8 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
   };
   if (intervals) {
     // 32 pixels x all steps per CTA; bins in windows of int32 accumulators
-    // sized for two CTAs per SM (one when a window would hold fewer than 256
-    // bins)
+    // sized for three CTAs per SM (FP32 geometry), else two, else one: the
+    // most CTAs whose windows still hold 256 bins (or all of them)
     t.ppt = 1;
     t.tile_cols = kIntervalTile;
     t.bin_groups = 1;
@@ -585,8 +585,12 @@ static dr_status plan_one(bool intervals, const dr_geometry *g, const double *wi
     const bool per_pixel = !rows_shared;
     const size_t fixed = (size_t)intervals_smem(K, t.kc * t.nchunks, B, 0, f64, per_pixel);
     const size_t per_bin = (size_t)kIntervalTile * 4;
-    size_t budget = (size_t)(kSmemPerSm / 2 - 1024);
-    if (fixed + per_bin * (size_t)std::min(B, 256) > budget) budget = (size_t)kSmemPerCtaMax;
+    const size_t want = fixed + per_bin * (size_t)std::min(B, 256);
+    p->iv_ctas = (!f64 && want <= (size_t)(kSmemPerSm / 3 - 1024)) ? 3
+                 : want <= (size_t)(kSmemPerSm / 2 - 1024)         ? 2
+                                                                    : 1;
+    const size_t budget = p->iv_ctas == 1 ? (size_t)kSmemPerCtaMax
+                                          : (size_t)(kSmemPerSm / p->iv_ctas - 1024);
     const long long win = fixed < budget ? (long long)((budget - fixed) / per_bin) : 0;
     if (win < std::min(B, 32)) {
       delete p;
@@ -844,6 +848,7 @@ static dr_status plan_parts(bool intervals, const dr_geometry *g, const double *
   top->kernel = f->kernel;
   top->pixel_groups = f->pixel_groups;
   top->window = f->window;
+  top->iv_ctas = f->iv_ctas;
   top->out_dtype = f->out_dtype;
   top->geom_prec = f->geom_prec;
   top->shift = f->shift;

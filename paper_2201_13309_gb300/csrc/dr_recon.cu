@@ -293,7 +293,9 @@ dr_status launch_pixels(const dr_plan_t *p, const CUtensorMap &tm, const uint16_
 template <class Geo, class OutT, bool kTma>
 dr_status launch_intervals(const dr_plan_t *p, const CUtensorMap &tm, const uint16_t *img,
                            void *out, cudaStream_t st) {
-  auto fn = intervals_kernel<Geo, OutT, kTma>;
+  constexpr bool kFx = std::is_same<Geo, GeoFx>::value;
+  auto fn = p->iv_ctas == 3 ? intervals_kernel<Geo, OutT, kTma, kFx ? 3 : 1>
+                            : intervals_kernel<Geo, OutT, kTma, kFx ? 2 : 1>;
   dr_status s = allow_smem((const void *)fn);
   if (s != DR_OK) return s;
   dim3 grid((p->cols + kIntervalTile - 1) / kIntervalTile, p->rows);
@@ -397,10 +399,14 @@ dr_status preload_kernels() {
       (const void *)check_kernel<false>,
       (const void *)check_kernel<true>,
       (const void *)groups_kernel,
-      (const void *)intervals_kernel<GeoFx, float, true>,
-      (const void *)intervals_kernel<GeoFx, float, false>,
-      (const void *)intervals_kernel<GeoFx, __nv_bfloat16, true>,
-      (const void *)intervals_kernel<GeoFx, __nv_bfloat16, false>,
+      (const void *)intervals_kernel<GeoFx, float, true, 2>,
+      (const void *)intervals_kernel<GeoFx, float, false, 2>,
+      (const void *)intervals_kernel<GeoFx, __nv_bfloat16, true, 2>,
+      (const void *)intervals_kernel<GeoFx, __nv_bfloat16, false, 2>,
+      (const void *)intervals_kernel<GeoFx, float, true, 3>,
+      (const void *)intervals_kernel<GeoFx, float, false, 3>,
+      (const void *)intervals_kernel<GeoFx, __nv_bfloat16, true, 3>,
+      (const void *)intervals_kernel<GeoFx, __nv_bfloat16, false, 3>,
   };
   for (const void *f : fns) {
     dr_status s = allow_smem(f);
