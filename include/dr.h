@@ -123,7 +123,8 @@ typedef struct {
   int32_t row_tables;       /* 1: the per-row (k, f) tables were built once at
                                plan time; 0: each tile builds its own */
   int32_t parts;            /* launches per reconstruction: monotone runs of
-                               the wire path x wire edges (1 for most scans) */
+                               the wire path (each cut into runs of at most
+                               2048 steps) x wire edges (1 for most scans) */
   double depth_min, depth_max;   /* range of all d_k (mm) */
   double min_step;               /* smallest |d_{k+1} - d_k| (mm) */
   size_t device_bytes;           /* device memory held by the plan */

@@ -926,7 +926,21 @@ extern "C" dr_status dr_plan(const dr_geometry *g, const double *wires, int32_t 
     set_error("dr_plan: the wire ends where it started along the beam (no travel)");
     return DR_ERR_GEOMETRY;
   }
-  const std::vector<int> one{0};
+  // Every kernel stages a tile's images for all the steps of a run in shared
+  // memory; a run of more steps than kMaxRunSteps is cut into parts that
+  // share their end steps (the apportioning is a sum over intervals, so the
+  // parts add up to the whole; later parts add to the output).
+  constexpr int kMaxRunSteps = 2048;
+  auto cut_long = [&](const std::vector<int> &s) {
+    std::vector<int> cut;
+    for (size_t r = 0; r < s.size(); ++r) {
+      const int k1 = r + 1 < s.size() ? s[r + 1] : K - 1;  // the run's last step
+      for (int k = s[r]; k < k1; k += kMaxRunSteps - 1) cut.push_back(k);
+    }
+    return cut;
+  };
+  const std::vector<int> one = cut_long({0});
+  starts = cut_long(starts);
   if (force_iv || repeated)
     return plan_parts(true, g, wires, K, edges, B, opt, one, travel, out);
   dr_status st = plan_parts(false, g, wires, K, edges, B, opt, starts, travel, out);

@@ -465,3 +465,27 @@ def test_maximum_size_sampled_rows():
         assert_parity(out[:, r:r + 1, :].cpu().numpy(), ref, host)
     del out, img
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("K,rotate,climb", [(2049, 0.0, False), (4300, 9.0, False),
+                                            (2600, 0.0, True)])
+def test_long_scans_in_parts(K, rotate, climb):
+    """Runs longer than 2048 steps are cut into parts that share their end
+    steps (the images of a tile are staged for all the steps of a part);
+    later parts add to the output.  Rows, per-pixel and interval kernels."""
+    rng = np.random.Generator(np.random.PCG64(K))
+    geom = synth.detector_geometry(3, 16, roi_origin=(1500, 900), det_rows=2048,
+                                   det_cols=2048, rotate_deg=rotate)
+    wires = synth.wire_path(K, dz=1e-4)
+    if climb:
+        wires[:, 1] += np.arange(K) * 0.00035 + rng.normal(0.0, 0.00004, K)
+    d = O.depths(geom, wires)
+    scat = synth.Scatterers(rng.uniform(d.min(), d.max(), 3), rng.uniform(500.0, 5000.0, 3))
+    images = synth.poisson_u16(rng, synth.expected_counts(geom, wires, scat, background=20.0))
+    sc = synth.Scan(geom, wires, synth.bin_edges(np.floor(d.min() * 1e3) - 2,
+                                                 np.ceil(d.max() * 1e3) + 2, 2.0), images)
+    plan, out = run(sc)
+    info = plan.info()
+    assert info["parts"] == -(-(K - 1) // 2047)
+    assert info["kernel"] == ("intervals" if climb else "pixels" if rotate else "rows")
+    assert_parity(out.cpu().numpy(), ref_of(sc), sc.images)
