@@ -432,9 +432,11 @@ void dr_server_destroy(dr_server_t *server);
  * see buffer sizes: d_images and d_out must hold the full [K][rows][cols] and
  * [B][rows][cols] arrays (the Python binding checks this).
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Each call writes its tables into a host
+ * The call cannot be captured into a CUDA graph: while stream is capturing
+ * it returns DR_ERR_UNSUPPORTED and queues nothing (a captured copy would
+ * keep reading the host buffer below, which later calls overwrite).  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current.  Each call writes its tables into a host
  * buffer inside the library and copies them into the array with an
  * asynchronous copy from that (pageable) buffer on stream: the copy first
  * waits for the work already queued on stream, and the call returns once

@@ -674,6 +674,15 @@ extern "C" dr_status dr_reconstruct_rows_static(const dr_geometry *g, const doub
     set_error("dr_reconstruct_rows_static: device %d out of range", dev);
     return DR_ERR_UNSUPPORTED;
   }
+  // a captured copy would keep reading the library's host buffer, which
+  // every later call overwrites: refuse to be captured
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+  if (e != cudaSuccess) return cuda_fail("dr_reconstruct_rows_static: cudaStreamIsCapturing", e);
+  if (cap != cudaStreamCaptureStatusNone) {
+    set_error("dr_reconstruct_rows_static: cannot be captured into a CUDA graph");
+    return DR_ERR_UNSUPPORTED;
+  }
   std::lock_guard<std::mutex> lk(g_static_mu);
   if (!g_static_dev[dev]) {
     void *ptr = nullptr;

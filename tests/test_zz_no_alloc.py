@@ -97,6 +97,34 @@ def test_static_entry_tables_just_under_the_limit():
     _check_close(got, ref.cpu().numpy(), images)
 
 
+def test_static_entry_refuses_stream_capture():
+    """Inside a stream capture the call returns DR_ERR_UNSUPPORTED and queues
+    nothing (the captured graph holds only the other work); the next call
+    outside the capture runs normally."""
+    a = synth.tiny_scan(23)
+    img = _dev(a.images)
+    out = torch.full((a.B, a.geom["rows"], a.geom["cols"]), float("nan"), device="cuda")
+    x = torch.zeros(1, device="cuda")
+    dr.reconstruct_rows_static(a.geom, a.wires, a.edges, img, out)  # device address looked up
+    torch.cuda.synchronize()
+    out.fill_(float("nan"))
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        x.add_(1.0)
+        with pytest.raises(dr.DrError) as ei:
+            dr.reconstruct_rows_static(a.geom, a.wires, a.edges, img, out)
+    assert ei.value.status == 8
+    assert "captured" in dr.lib().dr_last_error().decode()
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x.item()) == 1.0
+    assert bool(torch.isnan(out).all())
+    dr.reconstruct_rows_static(a.geom, a.wires, a.edges, img, out)
+    torch.cuda.synchronize()
+    _check_close(out.cpu().numpy(), _oracle(a), a.images)
+
+
 def _call_c(geom, wires, edges):
     """The C entry point itself, with null buffers (it must reject the
     request before it looks at them)."""
