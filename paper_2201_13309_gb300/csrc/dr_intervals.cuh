@@ -139,17 +139,33 @@ __device__ __forceinline__ bool intervals_tile(const CUtensorMap *tmap, const ui
     return biased(simg[DR_IDX((rev ? K - 1 - m : m) * TC + lc, Kpad * TC, c.err)]);
   };
   auto step_dI = [&](int m) { return (int)__fsub_rn(step_V(m), step_V(m + 1)); };
+  constexpr bool kFx = std::is_same<Geo, GeoFx>::value;
+  // intervals apportioned by themselves: zero length, and with FP32
+  // positions anything shorter than kMinStepUnits
+  auto is_short = [](pos_t a, pos_t b) {
+    if constexpr (kFx) return (uint32_t)(a < b ? b - a : a - b) < (uint32_t)kMinStepUnits;
+    return !(a < b) && !(b < a);
+  };
+  // b lies above a by an interval that is not short
+  auto longer = [](pos_t a, pos_t b) {
+    if constexpr (kFx) return b - a >= (pos_t)kMinStepUnits;
+    return a < b;
+  };
   // this thread's chunk of consecutive intervals m0 .. m1 - 1 of pixel lc
-  // (one chunk per slot: C * nw >= K - 1), its range of depths, and M =
-  // sum_k |dI_k| of each pixel (the chunks' sums, one atomic per chunk)
+  // (one chunk per slot: C * nw >= K - 1), its range of depths, whether it
+  // is a single run, and M = sum_k |dI_k| of each pixel (the chunks' sums,
+  // one atomic per chunk)
   const int C = (K - 1 + nw - 1) / nw;
   const int m0 = warp * C, m1 = min(m0 + C, K - 1);
   const bool has_chunk = valid && m0 < m1;
   pos_t cmin = 0, cmax = 0;
+  int one_run = 0;  // the chunk is one run with no short interval: 1 rising, 2 falling
   if (has_chunk) {
     uint32_t part = 0u;
     float Vp = step_V(m0);
     cmin = cmax = spos[DR_IDX(m0 * PS + lcs, K * PS, c.err)];
+    pos_t dp = cmin;
+    bool rise = true, fall = true;
     for (int m = m0; m < m1; ++m) {
       const float Vn = step_V(m + 1);
       part += (uint32_t)abs((int)__fsub_rn(Vp, Vn));
@@ -157,7 +173,11 @@ __device__ __forceinline__ bool intervals_tile(const CUtensorMap *tmap, const ui
       const pos_t d = spos[DR_IDX((m + 1) * PS + lcs, K * PS, c.err)];
       cmin = d < cmin ? d : cmin;
       cmax = d > cmax ? d : cmax;
+      rise = rise && longer(dp, d);
+      fall = fall && longer(d, dp);
+      dp = d;
     }
+    one_run = rise ? 1 : fall ? 2 : 0;
     if (part) atomicAdd(&ssum[lc], part);
   }
   // number of edges e_i <= x (0..B+1): a guess from the mean bin width,
@@ -182,18 +202,6 @@ __device__ __forceinline__ bool intervals_tile(const CUtensorMap *tmap, const ui
     return lo;
   };
 
-  constexpr bool kFx = std::is_same<Geo, GeoFx>::value;
-  // intervals apportioned by themselves: zero length, and with FP32
-  // positions anything shorter than kMinStepUnits
-  auto is_short = [](pos_t a, pos_t b) {
-    if constexpr (kFx) return (uint32_t)(a < b ? b - a : a - b) < (uint32_t)kMinStepUnits;
-    return !(a < b) && !(b < a);
-  };
-  // b lies above a by an interval that is not short
-  auto longer = [](pos_t a, pos_t b) {
-    if constexpr (kFx) return b - a >= (pos_t)kMinStepUnits;
-    return a < b;
-  };
   float q_scale = 0.f;  // 2^q of pixel lc, read once the sums are complete
   // Interval m of pixel lc by itself, dI != 0, into the bins of the window
   // [wb0, wb1).  A zero-length interval puts dI into the bin [e_j, e_{j+1})
@@ -284,6 +292,36 @@ __device__ __forceinline__ bool intervals_tile(const CUtensorMap *tmap, const ui
       };
       const float scale = up ? q_scale : -q_scale;  // the run's sign and the pixel's grid
       const int j0 = max(count_le(lo_run) - 1, wb0);
+      if constexpr (kFx) {
+        // bins j0 .. j1 - 1: those of the window whose lower edge lies below
+        // the run's end.  Every upper edge e_{j+1} lies above the run's start
+        // (e_{j0 + 1} > D(0), or e_{wb0} > D(0) when the run starts below
+        // the window) and so above t0, and a bin's part is added whether or
+        // not it is zero (one atomic, no branch)
+        const int j1 = min(count_le(hi_run - 1), wb1);
+        float g0 = G(sedge[DR_IDX(j0, B + 1, c.err)]);
+        int32_t *pa = acc + (j0 - wb0) * TC + lc;
+        for (int j = j0; j < j1; ++j, pa += TC) {
+          const pos_t e = sedge[DR_IDX(j + 1, B + 1, c.err)];
+          const pos_t ec = e < hi_run ? e : hi_run;
+          while (t1 < ec) {  // stops at the last point: t1 = D(len) >= ec
+            t0 = t1;
+            pd += ds;
+            t1 = *DR_PTR(pd, spos, K * PS, c.err);
+            pv += vs;
+            const float Vn = biased(*DR_PTR(pv, simg, Kpad * TC, c.err));
+            base = __fsub_rn(V0, V1);
+            d = __fsub_rn(V1, Vn);
+            V1 = Vn;
+            inv = iv_inv_len(t0, t1);
+          }
+          const float g1 = __fmaf_rn(iv_frac(ec, t0, inv), d, base);
+          atomicAdd(DR_PTR(pa, acc, window * TC, c.err),
+                    __float2int_rn(__fmul_rn(__fsub_rn(g1, g0), scale)));
+          g0 = g1;
+        }
+        return;
+      }
       const pos_t *pe = sedge + j0;
       int32_t *pa = acc + (j0 - wb0) * TC + lc;
       int32_t *const pa_end = acc + (wb1 - wb0) * TC;
@@ -303,24 +341,28 @@ __device__ __forceinline__ bool intervals_tile(const CUtensorMap *tmap, const ui
     // FP64 depths)
     const pos_t margin = kFx ? (pos_t)kMinStepUnits : (pos_t)0;
     if (has_chunk && cmax + margin >= ewlo && cmin - margin < ewhi) {
-      for (int m = m0; m < m1;) {
-        const pos_t a = spos[DR_IDX(m * PS + lcs, K * PS, c.err)],
-                    b = spos[DR_IDX((m + 1) * PS + lcs, K * PS, c.err)];
-        if (is_short(a, b)) {
-          const int dI = step_dI(m);
-          if (dI != 0) short_interval(m, a, dI, wb0, wb1);
-          ++m;
-          continue;
+      if (one_run) {  // the split below would find the one run
+        iv_run(m0, m1, one_run == 1);
+      } else {
+        for (int m = m0; m < m1;) {
+          const pos_t a = spos[DR_IDX(m * PS + lcs, K * PS, c.err)],
+                      b = spos[DR_IDX((m + 1) * PS + lcs, K * PS, c.err)];
+          if (is_short(a, b)) {
+            const int dI = step_dI(m);
+            if (dI != 0) short_interval(m, a, dI, wb0, wb1);
+            ++m;
+            continue;
+          }
+          const bool up = a < b;
+          int n = m + 1;  // the run: intervals m .. n - 1
+          for (pos_t prev = b; n < m1; ++n) {
+            const pos_t nx = spos[DR_IDX((n + 1) * PS + lcs, K * PS, c.err)];
+            if (!(up ? longer(prev, nx) : longer(nx, prev))) break;
+            prev = nx;
+          }
+          iv_run(m, n, up);
+          m = n;
         }
-        const bool up = a < b;
-        int n = m + 1;  // the run: intervals m .. n - 1
-        for (pos_t prev = b; n < m1; ++n) {
-          const pos_t nx = spos[DR_IDX((n + 1) * PS + lcs, K * PS, c.err)];
-          if (!(up ? longer(prev, nx) : longer(nx, prev))) break;
-          prev = nx;
-        }
-        iv_run(m, n, up);
-        m = n;
       }
     }
     __syncthreads();
