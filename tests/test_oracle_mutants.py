@@ -35,6 +35,16 @@ MUTANTS = {
     "no projection of the pixel": (C, "  perp(qo, f->axis, qp);", "  memcpy(qp, qo, sizeof qp);"),
     "last interval dropped": (C, "  for (int k = 0; k + 1 < K; ++k) {\n    if (dI[k] == 0) continue;",
                               "  for (int k = 0; k + 2 < K; ++k) {\n    if (dI[k] == 0) continue;"),
+    "interval ends not ordered": (C, "double lo = d[k] < d[k + 1] ? d[k] : d[k + 1];",
+                                  "double lo = d[k];"),
+    "zero-length interval dropped": (C, "if (j >= 0) out[(size_t)j * stride] += (double)dI[k];",
+                                     "if (j >= 0 && 0) out[(size_t)j * stride] += (double)dI[k];"),
+    "edge counted in the lower bin": (C, "if (e[mid] <= x) lo = mid; else hi = mid;",
+                                      "if (e[mid] < x) lo = mid; else hi = mid;"),
+    "overlap over the bin width": (C, "(double)dI[k] * (b - a) / (hi - lo);",
+                                   "(double)dI[k] * (b - a) / (e[j + 1] - e[j]);"),
+    "overlap end not clipped": (C, "double b = hi < e[j + 1] ? hi : e[j + 1];",
+                                "double b = hi < e[j + 1] ? e[j + 1] : hi;"),
     "both edges summed, not averaged": (PY, "return 0.5 * (reconstruct(",
                                         "return 1.0 * (reconstruct("),
     "both edges: trailing twice": (PY, '+ reconstruct(geom, wires, images, edges, "trailing"',
