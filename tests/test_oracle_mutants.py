@@ -45,6 +45,22 @@ MUTANTS = {
                                    "(double)dI[k] * (b - a) / (e[j + 1] - e[j]);"),
     "overlap end not clipped": (C, "double b = hi < e[j + 1] ? hi : e[j + 1];",
                                 "double b = hi < e[j + 1] ? e[j + 1] : hi;"),
+    "beam direction not normalised": (C, "double b[3] = {g[3] / nb, g[4] / nb, g[5] / nb};",
+                                      "double b[3] = {g[3], g[4], g[5]};"),
+    "wire axis not normalised": (C, "f->axis[i] = g[15 + i] / na;", "f->axis[i] = g[15 + i];"),
+    "travel from the first step": (C, "double move[3] = {wires[3 * (K - 1)] - wires[0], "
+                                      "wires[3 * (K - 1) + 1] - wires[1],\n"
+                                      "                    wires[3 * (K - 1) + 2] - wires[2]};",
+                                   "double move[3] = {wires[3] - wires[0], wires[4] - wires[1],\n"
+                                   "                    wires[5] - wires[2]};"),
+    "depth over |b'| instead of b'.b'": (C, "d[s] = dot3(x, f->bproj) / f->bb;",
+                                         "d[s] = dot3(x, f->bproj) / sqrt(f->bb);"),
+    "rows and columns swapped": (C, "q[i] = g[6 + i] + r * g[9 + i] + c * g[12 + i];",
+                                 "q[i] = g[6 + i] + c * g[9 + i] + r * g[12 + i];"),
+    "wire not taken relative to the beam origin": (
+        C, "double co[3] = {c[0] - f->origin[0], c[1] - f->origin[1], c[2] - f->origin[2]};",
+        "double co[3] = {c[0], c[1], c[2]};"),
+    "lower depth taken from one tangent": (C, "*lo = d[0] < d[1] ? d[0] : d[1];", "*lo = d[0];"),
     "both edges summed, not averaged": (PY, "return 0.5 * (reconstruct(",
                                         "return 1.0 * (reconstruct("),
     "both edges: trailing twice": (PY, '+ reconstruct(geom, wires, images, edges, "trailing"',

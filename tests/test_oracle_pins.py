@@ -4,7 +4,8 @@ Each pin checks the oracle against something it does not compute itself:
 brute-force ray-cylinder occlusion from the forward model, the exact
 quadratic solution of the tangent condition, the far-detector limit, fine
 subdivision of the depth intervals, conservation of the total intensity
-change, rigid-motion invariance, and noise-free forward-model scans.
+change, rigid-motion invariance, invariance to the lengths of the direction
+vectors and the sense of the wire axis, and noise-free forward-model scans.
 """
 import math
 
@@ -376,3 +377,54 @@ def test_both_edges_hand_computed():
     assert np.abs(got_l - lead).max() < tol
     assert np.abs(got_t - trail).max() < tol
     assert np.abs(got_b - 0.5 * (lead + trail)).max() < tol
+
+
+def test_depths_do_not_depend_on_direction_lengths_or_axis_sense():
+    """The beam and the wire axis enter as directions only: scaling either
+    vector, or reversing the wire axis (the same line), leaves every depth of
+    both edges unchanged.  A rotated, tilted detector with an oblique wire
+    axis and an oblique beam, so that no component is trivially zero."""
+    g = S.detector_geometry(4, 5, rotate_deg=7.0, tilt_deg=4.0)
+    g["wire_axis"] = [1.0, 0.05, -0.03]
+    g["beam_dir"] = [0.02, 0.01, 1.0]
+    wires = S.wire_path(9)
+    base = {e: O.depths(g, wires, e) for e in ("leading", "trailing")}
+    assert not np.allclose(base["leading"], base["trailing"])
+    for key, f in (("beam_dir", 2.5), ("beam_dir", 0.01), ("wire_axis", 0.3),
+                   ("wire_axis", -1.0), ("wire_axis", -4.0)):
+        h = dict(g)
+        h[key] = [f * v for v in g[key]]
+        for e in base:
+            got = O.depths(h, wires, e)
+            assert np.abs(got - base[e]).max() < 1e-10, (key, f, e)
+
+
+def test_leading_edge_follows_the_net_travel():
+    """A path whose first step goes backwards (0.4 of a step) before the
+    forward sweep.  The leading edge is the end that moves with the wire's
+    net travel, so the forward sweep still hides a noise-free scatterer with
+    its leading edge: the scatterer depth lies in the leading-edge interval
+    of the step that hides it (brute-force occlusion of the forward model),
+    that interval's bins get +A, and the first interval runs backwards."""
+    geom = S.detector_geometry(3, 2, roi_origin=(30, 0), det_rows=64, det_cols=64)
+    fwd = S.wire_path(41)
+    wires = np.concatenate([fwd[:1] + 0.4 * (fwd[1] - fwd[0]), fwd])
+    e = S.bin_edges(-50, 50, 1.0)
+    A = 1000.0
+    d = O.depths(geom, wires)
+    assert (d[:, :, 1] < d[:, :, 0]).all() and (np.diff(d[:, :, 1:], axis=2) > 0).all()
+    for s in (0.0101, 0.0233):
+        scat = S.Scatterers(np.array([s]), np.array([A]))
+        images = np.rint(S.expected_counts(geom, wires, scat)).astype(np.uint16)
+        out = O.reconstruct(geom, wires, images, e)
+        for r in range(3):
+            vis = images[:, r, 0] > 0
+            kstar = int(np.argmin(vis))                 # first hidden step
+            assert kstar > 1 and vis[:kstar].all() and not vis[kstar:].any()
+            lo, hi = d[r, 0, kstar - 1], d[r, 0, kstar]
+            assert lo <= s <= hi
+            jlo = int(np.searchsorted(e, lo, "right") - 1)
+            jhi = int(np.searchsorted(e, hi, "right") - 1)
+            col = out[:, r, 0]
+            assert col[jlo:jhi + 1].sum() == pytest.approx(A, abs=1e-9)
+            assert np.abs(col).sum() == pytest.approx(A, abs=1e-9)
