@@ -22,7 +22,8 @@
 // line of its output plane.  The bins go through shared-memory windows of
 // `window` int32 accumulators per pixel.
 // Each thread splits its chunk into strictly monotone runs (and zero-length
-// intervals) and walks each run once over the bins it spans.  Over one run
+// intervals) and walks each run once over the bins it spans; a chunk that
+// its first pass finds to be a single run is walked without the split.  Over one run
 // the sum of dI_k * phi_k at an edge e is s * G(e) with G(e) = V_0 - V(e):
 // V interpolates the run's image values linearly in depth (clamped at both
 // ends of the run), V_0 is the value at its shallowest point, and s = +1 when
