@@ -61,6 +61,9 @@ MUTANTS = {
         C, "double co[3] = {c[0] - f->origin[0], c[1] - f->origin[1], c[2] - f->origin[2]};",
         "double co[3] = {c[0], c[1], c[2]};"),
     "lower depth taken from one tangent": (C, "*lo = d[0] < d[1] ? d[0] : d[1];", "*lo = d[0];"),
+    "row offset ignored (reconstruction)": (C, "int r = J->r0 + rr;", "int r = rr;"),
+    "row offset ignored (depths)": (C, "st = pixel_depths(geom, &f, wires, K, edge, r0 + r, c,",
+                                    "st = pixel_depths(geom, &f, wires, K, edge, r, c,"),
     "both edges summed, not averaged": (PY, "return 0.5 * (reconstruct(",
                                         "return 1.0 * (reconstruct("),
     "both edges: trailing twice": (PY, '+ reconstruct(geom, wires, images, edges, "trailing"',

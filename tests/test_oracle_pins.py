@@ -428,3 +428,35 @@ def test_leading_edge_follows_the_net_travel():
             col = out[:, r, 0]
             assert col[jlo:jhi + 1].sum() == pytest.approx(A, abs=1e-9)
             assert np.abs(col).sum() == pytest.approx(A, abs=1e-9)
+
+
+def test_row_offsets_follow_the_forward_model():
+    """Rows asked for by offset (r0, nrows) are those rows of the detector.
+    Three rows 5 mm apart along z (their depth sequences about 5 um apart), one
+    noise-free scatterer: each row is hidden at the step that the forward
+    model's brute-force occlusion gives for that row, its depths asked for
+    alone put the scatterer in that step's leading-edge interval, and its
+    reconstruction asked for alone puts +A on that interval's bins."""
+    geom = S.detector_geometry(3, 1)
+    geom["det_origin"] = [0.0, S.DET_Y_MM, -5.0]
+    geom["row_step"] = [0.0, 0.0, 5.0]
+    wires = S.wire_path(41)
+    e = S.bin_edges(-50, 50, 1.0)
+    A, s = 1000.0, 0.0201
+    images = np.rint(S.expected_counts(geom, wires, S.Scatterers(np.array([s]),
+                                                                 np.array([A])))).astype(np.uint16)
+    hidden_at = []
+    for r in range(3):
+        vis = images[:, r, 0] > 0
+        kstar = int(np.argmin(vis))                     # first hidden step
+        assert kstar > 0 and vis[:kstar].all() and not vis[kstar:].any()
+        hidden_at.append(kstar)
+        d = O.depths(geom, wires, r0=r, nrows=1)[0, 0]
+        lo, hi = d[kstar - 1], d[kstar]
+        assert lo <= s <= hi
+        col = O.reconstruct(geom, wires, images, e, r0=r, nrows=1)[:, 0, 0]
+        jlo = int(np.searchsorted(e, lo, "right") - 1)
+        jhi = int(np.searchsorted(e, hi, "right") - 1)
+        assert col[jlo:jhi + 1].sum() == pytest.approx(A, abs=1e-9)
+        assert np.abs(col).sum() == pytest.approx(A, abs=1e-9)
+    assert len(set(hidden_at)) == 3                     # the rows are told apart
