@@ -64,6 +64,10 @@ MUTANTS = {
     "row offset ignored (reconstruction)": (C, "int r = J->r0 + rr;", "int r = rr;"),
     "row offset ignored (depths)": (C, "st = pixel_depths(geom, &f, wires, K, edge, r0 + r, c,",
                                     "st = pixel_depths(geom, &f, wires, K, edge, r, c,"),
+    "no refusal of a beam met before the wire": (
+        C, "if (!(t > sqrt(D * D - f->radius * f->radius))) return OR_BAD_GEOMETRY;", ";"),
+    "no refusal of a path without travel": (
+        C, "if (along == 0.0) return OR_BAD_GEOMETRY; /* no travel along the beam */", ";"),
     "both edges summed, not averaged": (PY, "return 0.5 * (reconstruct(",
                                         "return 1.0 * (reconstruct("),
     "both edges: trailing twice": (PY, '+ reconstruct(geom, wires, images, edges, "trailing"',

@@ -38,7 +38,7 @@ def _leading_boundary_bisect(q, centre, axis=(1.0, 0.0, 0.0), radius=R,
         return bool(S.hidden_by_wire(bo + d * bd, qa, centre, axis, radius)[0])
 
     grid = np.arange(-3.0, 3.0, 2e-4)
-    hid = np.array([hidden(d) for d in grid])
+    hid = S.hidden_by_wire(bo[None, :] + grid[:, None] * bd[None, :], qa, centre, axis, radius)
     assert hid.any(), "wire hides nothing from this pixel"
     i = int(np.nonzero(hid)[0].max())
     a, b = grid[i], grid[i] + 2e-4
@@ -460,3 +460,41 @@ def test_row_offsets_follow_the_forward_model():
         assert col[jlo:jhi + 1].sum() == pytest.approx(A, abs=1e-9)
         assert np.abs(col).sum() == pytest.approx(A, abs=1e-9)
     assert len(set(hidden_at)) == 3                     # the rows are told apart
+
+
+def _refused(geom, wires, edges=None, images=None):
+    edges = S.bin_edges(-50, 50, 1.0) if edges is None else edges
+    if images is None:
+        images = np.zeros((len(wires), geom["rows"], geom["cols"]), np.uint16)
+    with pytest.raises(O.OracleError) as ei:
+        O.reconstruct(geom, wires, images, edges)
+    return str(ei.value)
+
+
+def test_degenerate_geometries_are_refused():
+    """Where the method has no answer the oracle refuses rather than guess:
+    a beam along the wire axis (no plane to project into), a wire path with
+    no travel along the beam (no leading edge), a pixel inside the wire, a
+    pixel whose tangent lines meet the beam before the wire (the wire then
+    hides nothing on the beam from it), bins that do not increase, fewer
+    than two steps."""
+    g = S.detector_geometry(2, 2)
+    w = S.wire_path(5)
+    along = dict(g, beam_dir=[1.0, 0.0, 0.0])
+    assert _refused(along, w) == "bad geometry"
+    still = w.copy()
+    still[:, 2] = still[0, 2]
+    still[:, 0] = np.arange(5) * 0.01               # moving along the axis only
+    assert _refused(g, still) == "bad geometry"
+    inside = S.detector_geometry(1, 1)
+    inside["det_origin"] = [0.0, S.WIRE_Y_MM, S.WIRE_Z0_MM + 0.002]
+    assert _refused(inside, w) == "bad geometry"
+    between = S.detector_geometry(1, 1)
+    between["det_origin"] = [0.0, 0.3, 0.0]         # below the wire, above the beam
+    assert _refused(between, w) == "bad geometry"
+    e = S.bin_edges(-50, 50, 1.0).copy()
+    e[7] = e[6]
+    assert _refused(g, w, edges=e) == "bad argument"
+    assert _refused(g, w[:1]) == "bad argument"
+    # and the regular geometry itself is accepted
+    O.reconstruct(g, w, np.zeros((5, 2, 2), np.uint16), S.bin_edges(-50, 50, 1.0))
