@@ -68,6 +68,13 @@ MUTANTS = {
         C, "if (!(t > sqrt(D * D - f->radius * f->radius))) return OR_BAD_GEOMETRY;", ";"),
     "no refusal of a path without travel": (
         C, "if (along == 0.0) return OR_BAD_GEOMETRY; /* no travel along the beam */", ";"),
+    "beam not projected onto the plane": (C, "perp(b, f->axis, f->bproj);",
+                                          "memcpy(f->bproj, b, sizeof b);"),
+    "one tangent taken twice": (C, "double th = s == 0 ? alpha : -alpha;", "double th = alpha;"),
+    "tangent parameter sign": (C, "double t = -dot3(qxb, f->axis) / den;",
+                               "double t = dot3(qxb, f->axis) / den;"),
+    "travel sign inverted": (C, "int lead_is_hi = f->travel > 0;", "int lead_is_hi = f->travel < 0;"),
+    "overlap start not clipped": (C, "double a = lo > e[j] ? lo : e[j];", "double a = e[j];"),
     "both edges summed, not averaged": (PY, "return 0.5 * (reconstruct(",
                                         "return 1.0 * (reconstruct("),
     "both edges: trailing twice": (PY, '+ reconstruct(geom, wires, images, edges, "trailing"',
