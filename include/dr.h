@@ -233,7 +233,12 @@ dr_status dr_reconstruct_streamed(const dr_plan_t *plan, const uint16_t *h_image
  * dr_reconstruct_selected: bins of the listed pixels only, compacted:
  *   d_out[j * n + i] is bin j of pixel d_index[i] (FP32 or BF16 per the plan),
  *   bitwise equal to dr_reconstruct's value for that pixel.  n is the host
- *   count of listed pixels. */
+ *   count of listed pixels; d_index holds n row-major pixel numbers in
+ *   increasing order, each in [0, rows * cols) (as dr_select_pixels writes
+ *   them).  A list with numbers outside the ROI or out of order makes the
+ *   kernels read nothing outside the images, but the output columns of
+ *   those numbers are undefined; where such a number reaches a kernel's
+ *   walk, the plan's error word records it (dr_plan_check: DR_ERR_CUDA). */
 dr_status dr_pixel_activity(const uint16_t *d_images, int32_t K, int32_t rows, int32_t cols,
                             float *d_activity, dr_stream_t stream);
 size_t dr_select_scratch_bytes(int64_t n);

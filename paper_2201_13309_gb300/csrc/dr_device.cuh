@@ -1274,6 +1274,10 @@ __global__ void __launch_bounds__(kSelThreads) selected_kernel(const Consts c, i
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int p = idx[i], K = c.K, B = c.B;
+  if ((unsigned)p >= (unsigned)(c.H * c.W)) {  // not a pixel of the ROI: reported, not read
+    atomicCAS(c.err, 0, kDevBounds | (__LINE__ << 4));
+    return;
+  }
   const size_t plane = (size_t)c.H * c.W;
   const int row = p / c.W;
   const bool rev = c.reverse != 0;
@@ -1439,6 +1443,10 @@ __global__ void __launch_bounds__(512) selected_rows_kernel(const __grid_constan
     const int il = sidx % m, g = sidx / m, i = lo + il;
     const int jb = (int)((long long)B * g / G), je = (int)((long long)B * (g + 1) / G);
     const int lc = idx[i] - row * c.W - c0;
+    if ((unsigned)lc >= (unsigned)min(TC, c.W - c0)) {  // a list not in increasing order
+      atomicCAS(c.err, 0, kDevBounds | (__LINE__ << 4));
+      continue;
+    }
     auto pxs = [&](int k) { return biased(simg[(size_t)(rev ? K - 1 - k : k) * TC + lc]); };
     const float I0 = pxs(0);
     OutT *o = out + (size_t)jb * n + i;

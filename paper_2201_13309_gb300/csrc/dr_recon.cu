@@ -586,7 +586,7 @@ extern "C" dr_status dr_plan_check(const dr_plan_t *p) {
   if (v != kDevOk) {
     e = cudaMemcpy(p->c.err, &zero, sizeof(zero), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail("dr_plan_check: clear", e);
-    if ((v & 15) == kDevBounds) {  // the bounds-checked build only
+    if ((v & 15) == kDevBounds) {  // the bounds-checked build, or a bad pixel list
       set_error("a kernel index was out of range (device source line %d)", v >> 4);
       return DR_ERR_CUDA;
     }

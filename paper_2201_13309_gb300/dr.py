@@ -209,6 +209,22 @@ def _dptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _require(t, what, shape=None, dtype=None, int16=False, cuda=True):
+    """Checks a tensor handed to the C ABI by address (the library cannot
+    see buffer sizes or types): its shape, element type, contiguity and
+    whether it lives in device or host memory.  ValueError before any call."""
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what} {tuple(t.shape)} != {tuple(shape)}")
+    if int16 and (t.element_size() != 2 or t.is_floating_point() or t.is_complex()):
+        raise ValueError(f"{what} must hold 16-bit integers, got {t.dtype}")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{what} dtype {t.dtype} != {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if bool(t.is_cuda) != cuda:
+        raise ValueError(f"{what} must be in {'device' if cuda else 'host'} memory")
+
+
 class Plan:
     """A reconstruction plan (dr_plan): geometry, wire path and bin edges.
 
@@ -281,6 +297,7 @@ class Plan:
 
     def reconstruct_host(self, h_images, h_out, d_images, d_out, stream=None):
         """End to end: pinned host images -> device -> reconstruct -> host."""
+        self._check_host(h_images, h_out)
         self._check_shapes(d_images, d_out)
         check(lib().dr_reconstruct_host(self._h, _dptr(h_images), _dptr(h_out),
                                         _dptr(d_images), _dptr(d_out),
@@ -290,10 +307,8 @@ class Plan:
     def reconstruct_streamed(self, h_images, h_out, workspace, slab_rows=0, stream=None):
         """Out-of-core form: host images -> row slabs through a device
         workspace (a CUDA tensor; three slab buffers) -> host output."""
-        if tuple(h_images.shape) != (self.K, self.rows, self.cols):
-            raise ValueError("h_images shape")
-        if tuple(h_out.shape) != (self.B, self.rows, self.cols):
-            raise ValueError("h_out shape")
+        self._check_host(h_images, h_out)
+        _require(workspace, "workspace")
         check(lib().dr_reconstruct_streamed(
             self._h, _dptr(h_images), _dptr(h_out), _dptr(workspace),
             workspace.numel() * workspace.element_size(), int(slab_rows),
@@ -302,13 +317,19 @@ class Plan:
 
     def reconstruct_selected(self, images, index, n=None, out=None, stream=None):
         """Bins of the listed pixels only: out [B, n], out[:, i] = bin values
-        of pixel index[i] (row-major).  n defaults to len(index)."""
+        of pixel index[i] (row-major; int32, each in [0, rows * cols)).  n
+        defaults to len(index)."""
         import torch
         n = int(index.numel() if n is None else n)
         if out is None:
             out = torch.empty((self.B, n), dtype=self.out_torch_dtype(), device=images.device)
-        if tuple(images.shape) != (self.K, self.rows, self.cols) or out.shape[1] < n:
-            raise ValueError("shape mismatch")
+        _require(images, "images", (self.K, self.rows, self.cols), int16=True)
+        _require(index, "index", dtype=torch.int32)
+        if index.dim() != 1 or not 0 <= n <= index.numel():
+            raise ValueError(f"index must be one-dimensional with at least n = {n} entries")
+        _require(out, "out", dtype=self.out_torch_dtype())
+        if out.dim() != 2 or out.shape[0] != self.B or (n > 0 and out.shape[1] != n):
+            raise ValueError(f"out {tuple(out.shape)} != {(self.B, n)}")
         check(lib().dr_reconstruct_selected(self._h, _dptr(images), _dptr(index), n,
                                             _dptr(out), ctypes.c_void_p(_stream_handle(stream))))
         return out
@@ -326,14 +347,13 @@ class Plan:
         check(lib().dr_plan_check(self._h))
 
     def _check_shapes(self, images, out):
-        if tuple(images.shape) != (self.K, self.rows, self.cols):
-            raise ValueError(f"images {tuple(images.shape)} != {(self.K, self.rows, self.cols)}")
-        if tuple(out.shape) != (self.B, self.rows, self.cols):
-            raise ValueError(f"out {tuple(out.shape)} != {(self.B, self.rows, self.cols)}")
-        if images.element_size() != 2 or not images.is_contiguous() or not out.is_contiguous():
-            raise ValueError("images must be contiguous 16-bit, out contiguous")
-        if out.dtype != self.out_torch_dtype():
-            raise ValueError(f"out dtype {out.dtype} != {self.out_torch_dtype()}")
+        _require(images, "images", (self.K, self.rows, self.cols), int16=True)
+        _require(out, "out", (self.B, self.rows, self.cols), dtype=self.out_torch_dtype())
+
+    def _check_host(self, h_images, h_out):
+        _require(h_images, "h_images", (self.K, self.rows, self.cols), int16=True, cuda=False)
+        _require(h_out, "h_out", (self.B, self.rows, self.cols), dtype=self.out_torch_dtype(),
+                 cuda=False)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -429,6 +449,10 @@ class Server:
         by the server object until the request is released."""
         w = np.ascontiguousarray(wires, dtype=np.float64)
         e = np.ascontiguousarray(edges, dtype=np.float64)
+        if w.ndim != 2 or w.shape[1] != 3 or e.ndim != 1 or e.shape[0] < 2:
+            raise ValueError(f"wires must be [K, 3] and edges [B + 1], got {w.shape}, {e.shape}")
+        _require(h_images, "h_images", (w.shape[0], int(geom["rows"]), int(geom["cols"])),
+                 int16=True, cuda=False)
         g = geometry_struct(geom, edge)
         rid = ctypes.c_uint64()
         check(lib().dr_server_submit(self._h, ctypes.byref(g), w.ctypes.data_as(ctypes.c_void_p),
@@ -484,6 +508,7 @@ def image_differences(images, stream=None):
     """int32 [K-1, rows, cols]: exact I_k - I_{k+1} as the kernels form it."""
     import torch
     K, H, W = images.shape
+    _require(images, "images", int16=True)
     d = torch.empty((max(K - 1, 0), H, W), dtype=torch.int32, device=images.device)
     check(lib().dr_image_differences(_dptr(images), K, H, W, _dptr(d),
                                      ctypes.c_void_p(_stream_handle(stream))))
@@ -539,6 +564,7 @@ def pixel_activity(images, stream=None):
     """float32 [rows, cols]: sum_k |I_k - I_{k+1}| per pixel (exact)."""
     import torch
     K, H, W = images.shape
+    _require(images, "images", int16=True)
     act = torch.empty((H, W), dtype=torch.float32, device=images.device)
     check(lib().dr_pixel_activity(_dptr(images), K, H, W, _dptr(act),
                                   ctypes.c_void_p(_stream_handle(stream))))
@@ -549,6 +575,7 @@ def select_pixels(activity, threshold, stream=None):
     """(int32 index tensor of the pixels with activity >= threshold, in
     increasing row-major order; their count)."""
     import torch
+    _require(activity, "activity", dtype=torch.float32)
     n = activity.numel()
     idx = torch.empty(max(n, 1), dtype=torch.int32, device=activity.device)
     cnt = torch.zeros(1, dtype=torch.int32, device=activity.device)

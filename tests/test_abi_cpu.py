@@ -119,3 +119,61 @@ def test_static_entry_binding_checks_buffers_before_any_call(monkeypatch):
     with pytest.raises(ValueError):
         dr.reconstruct_rows_static(sc.geom, sc.wires, sc.edges, img, good_out,
                                    status=torch.zeros(2, dtype=torch.int32))
+
+
+def _unbuilt_plan(K, rows, cols, B, out_dtype="f32"):
+    """A Plan object with the attributes its methods check, but no library
+    plan behind it (dr_plan needs a GPU)."""
+    p = object.__new__(dr.Plan)
+    p._h = ctypes.c_void_p()
+    p.K, p.rows, p.cols, p.B, p.out_dtype = K, rows, cols, B, out_dtype
+    return p
+
+
+def test_binding_checks_buffers_before_any_call(monkeypatch):
+    """Every entry point that hands the library a buffer by address checks
+    its shape, element type, contiguity and memory (device or host) first:
+    a wrong one raises ValueError and the library is never called."""
+    import torch
+
+    def no_call():
+        raise AssertionError("the library was called")
+
+    monkeypatch.setattr(dr, "lib", no_call)
+    K, H, W, B = 5, 4, 8, 11
+    p = _unbuilt_plan(K, H, W, B)
+    img = torch.zeros((K, H, W), dtype=torch.int16)
+    out = torch.zeros((B, H, W), dtype=torch.float32)
+    bad = [
+        lambda: p.reconstruct(img, out),                                    # host tensors
+        lambda: p.reconstruct(torch.zeros((K, H, W + 1), dtype=torch.int16), out),
+        lambda: p.reconstruct(img.float(), out),
+        lambda: p.reconstruct(img, out.double()),
+        lambda: p.reconstruct(img, out.transpose(1, 2).contiguous().transpose(1, 2)),
+        lambda: p.reconstruct_host(img, out.half(), img, out),              # host output type
+        lambda: p.reconstruct_host(img, torch.zeros((B, H, W - 1)), img, out),
+        lambda: p.reconstruct_host(img, out, img, out),                     # "device" on host
+        lambda: p.reconstruct_streamed(img, out.half(), torch.zeros(64, dtype=torch.uint8)),
+        lambda: p.reconstruct_streamed(img[:, :, ::2], out, torch.zeros(64, dtype=torch.uint8)),
+        lambda: p.reconstruct_streamed(img, out, torch.zeros(64, dtype=torch.uint8)),
+        lambda: p.reconstruct_selected(torch.zeros((K, H, W - 1), dtype=torch.int16),
+                                       torch.zeros(3, dtype=torch.int32), 3),
+        lambda: dr.image_differences(img.float()),
+        lambda: dr.image_differences(img),
+        lambda: dr.pixel_activity(img[:, :, ::2]),
+        lambda: dr.select_pixels(torch.zeros(16, dtype=torch.float64), 0.5),
+        lambda: dr.select_pixels(torch.zeros(16), 0.5),
+    ]
+    for i, f in enumerate(bad):
+        with pytest.raises(ValueError):
+            f()
+    srv = object.__new__(dr.Server)
+    srv._h, srv._pinned = ctypes.c_void_p(), {}
+    sc = synth.tiny_scan(3, rows=H, cols=W, K=K)
+    for h in (torch.zeros((K - 1, H, W), dtype=torch.int16),
+              torch.zeros((K, H, W), dtype=torch.float32),
+              torch.zeros((K, W, H), dtype=torch.int16).transpose(1, 2)):
+        with pytest.raises(ValueError):
+            srv.submit(sc.geom, sc.wires, sc.edges, h)
+    with pytest.raises(ValueError):
+        srv.submit(sc.geom, sc.wires.reshape(-1), sc.edges, torch.zeros((K, H, W), dtype=torch.int16))
