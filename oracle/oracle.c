@@ -33,7 +33,10 @@
  * Parity is pinned (tests/test_oracle_pins.py) against brute-force
  * ray-cylinder occlusion, the exact quadratic solution of the tangent
  * condition, the far-detector limit d = z + R, fine subdivision of the
- * intervals, conservation, and noise-free forward-model scans.
+ * intervals, conservation, invariance to the lengths of the direction
+ * vectors and the sense of the wire axis, noise-free forward-model scans
+ * (also for a path whose first step runs backwards and for rows asked for
+ * by offset), and the refusal of geometries where the method has no answer.
  */
 #include <math.h>
 #include <pthread.h>
